@@ -1,0 +1,156 @@
+/*
+ * panda.h -- C ABI of the GB300 (sm_103a) kd-tree build and exact KNN library.
+ *
+ * The method is PANDA's local kd-tree construction and k-nearest-neighbour
+ * query (Patwary et al., arXiv 1607.08220): Sec. III-A (steps ii-iv: split
+ * levels, bucket stop, leaf packing), Sec. III-A1 (split dimension by maximum
+ * sample variance, split value by a sampled histogram, bucket size B) and
+ * Algorithm 1 in Sec. III-B/III-C (stack traversal with a top-k heap and
+ * bound pruning).  The problem statement followed here is Algorithm 1's
+ * signature FINDKNN(T, q, k, r) with r = infinity.
+ *
+ * Result contract (every entry point that returns neighbours):
+ *   - d2(q, x) is the FP32 sum over dimensions 0..d-1, in that order, of
+ *     fl(fl(q_i - x_i) * fl(q_i - x_i)), every operation rounded to nearest
+ *     even, no fused multiply-add, denormals kept;
+ *   - row r of the output lists the k points with the smallest keys
+ *     (d2, point index), ascending; ids are the 0-based row indices of the
+ *     points given to the build; the answer is unique;
+ *   - when the tree holds n < k points, entries n..k-1 of a row are
+ *     (id -1, d2 +inf).
+ *
+ * Conventions:
+ *   - Functions without the _host suffix take DEVICE pointers (CUDA global
+ *     memory of the current device); a host pointer is rejected with
+ *     PANDA_ERR_INVALID_ARGUMENT.  _host variants take host pointers
+ *     (pinned or pageable) and copy in and out themselves.
+ *   - `stream` arguments are cudaStream_t values passed as void*; NULL is
+ *     the legacy default stream.
+ *   - Outputs are caller-allocated.  No exception crosses this ABI.  On any
+ *     error the outputs are unspecified and the tree handle is not created.
+ *   - Every CUDA failure is reported as PANDA_ERR_CUDA; panda_last_error()
+ *     returns the message of the last failure on the calling thread.
+ *   - A tree is immutable after its build: concurrent panda_knn calls on one
+ *     tree from several streams are allowed.  panda_free must not run while
+ *     work that reads the tree is in flight.
+ *   - Valid ranges: 1 <= n < 2^31, 1 <= d <= 16, 1 <= bucket <= 256,
+ *     1 <= k <= 64, m >= 0 (m = 0 does nothing).  Out-of-range values give
+ *     PANDA_ERR_INVALID_ARGUMENT (or PANDA_ERR_UNSUPPORTED for d > 16,
+ *     k > 64, bucket > 256).  Coordinates must be finite
+ *     (PANDA_ERR_NONFINITE_INPUT otherwise).
+ */
+#ifndef PANDA_H
+#define PANDA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct panda_tree panda_tree; /* opaque; owns its device memory */
+
+typedef enum panda_status {
+    PANDA_OK = 0,
+    PANDA_ERR_INVALID_ARGUMENT = 1,
+    PANDA_ERR_NONFINITE_INPUT = 2,
+    PANDA_ERR_UNSUPPORTED = 3,
+    PANDA_ERR_OUT_OF_MEMORY = 4,
+    PANDA_ERR_CUDA = 5,
+    PANDA_ERR_TIMEOUT = 6,
+    PANDA_ERR_QUEUE_FULL = 7,
+    PANDA_ERR_DEPTH = 8 /* a node deeper than 64 levels would still hold > bucket points */
+} panda_status;
+
+/* Query point ordering before the traversal (does not change results). */
+typedef enum panda_order {
+    PANDA_ORDER_NONE = 0,   /* queries traversed in input order */
+    PANDA_ORDER_MORTON = 1, /* grouped by a 30-bit Morton code over the tree's root box */
+    PANDA_ORDER_LEAF = 2    /* grouped by the leaf bucket each query falls in */
+} panda_order;
+
+typedef struct panda_query_params {
+    int32_t order;           /* panda_order; default PANDA_ORDER_LEAF */
+    int32_t lanes_per_query; /* 1 (default); reserved for split leaf scans */
+} panda_query_params;
+
+typedef struct panda_tree_info {
+    int64_t n;          /* points */
+    int32_t d;          /* dimensions */
+    int32_t bucket;     /* B: maximum points per leaf */
+    int64_t num_nodes;  /* inner + leaf nodes */
+    int64_t num_leaves;
+    int32_t depth;      /* deepest node (root = 0) */
+    int32_t node_floats;  /* floats per node record (header + box, padded to 4) */
+    int32_t point_floats; /* floats per packed point (coordinates + id, padded to 4) */
+    int32_t subtree_threshold; /* nodes of at most this many points were built in shared memory */
+    int64_t device_bytes;      /* device memory held by the tree */
+} panda_tree_info;
+
+/* ---- construction: Sec. III-A (ii)-(iv) and Sec. III-A1 --------------------
+ * points: device, row-major [n][d] FP32.  Copied into the tree (leaf order,
+ * one packed record per point), so the caller may free it once the call
+ * returns (for _async: once `stream` has passed the build).
+ * bucket: B, the leaf capacity (the paper's best value is 32).
+ * The build synchronises `stream` once, between its data-parallel levels and
+ * its shared-memory subtree stage, to size the latter. */
+panda_status panda_build(const float* points, int64_t n, int32_t d, int32_t bucket,
+                         panda_tree** out);
+panda_status panda_build_async(const float* points, int64_t n, int32_t d, int32_t bucket,
+                               void* stream, panda_tree** out);
+/* Same with host `points`; copies host->device inside the call. */
+panda_status panda_build_host(const float* points, int64_t n, int32_t d, int32_t bucket,
+                              void* stream, panda_tree** out);
+
+/* ---- query: Algorithm 1 (corrected), Sec. III-B/III-C ------------------------
+ * queries: device [m][d] FP32 (d = the tree's d); out_ids: device [m][k] int32;
+ * out_d2: device [m][k] FP32.  panda_knn blocks until the results are written;
+ * panda_knn_async only enqueues on `stream` (params may be NULL for defaults).
+ * The query uses a temporary device workspace of about 12*m bytes for the
+ * query ordering (from the stream-ordered pool; freed in stream order). */
+panda_status panda_knn(const panda_tree* tree, const float* queries, int64_t m, int32_t k,
+                       int32_t* out_ids, float* out_d2);
+panda_status panda_knn_async(const panda_tree* tree, const float* queries, int64_t m, int32_t k,
+                             int32_t* out_ids, float* out_d2,
+                             const panda_query_params* params, void* stream);
+/* Same with host queries/outputs; copies in and out inside the call and returns
+ * after the results are on the host. */
+panda_status panda_knn_host(const panda_tree* tree, const float* queries, int64_t m, int32_t k,
+                            int32_t* out_ids, float* out_d2, const panda_query_params* params,
+                            void* stream);
+
+/* Releases the tree's device memory (NULL-safe). */
+void panda_free(panda_tree* tree);
+
+/* ---- inspection -------------------------------------------------------------
+ * panda_tree_get_info fills *info.  panda_tree_copy copies the tree's node
+ * records ([num_nodes][node_floats] floats) and packed points
+ * ([n][point_floats] floats) to host buffers of those sizes (either may be
+ * NULL).  Node record: int32 a, int32 b, float split, uint32 meta, then lo[d],
+ * hi[d], zero padding; meta bit 31 = leaf, bit 30 = index split, bits 0..4 =
+ * split dimension; an inner node's children are a and a+1; a leaf holds the
+ * packed points a .. a+b-1.  Packed point: coordinates, then the point's id
+ * as int32 bits in float slot d, zero padding. */
+panda_status panda_tree_get_info(const panda_tree* tree, panda_tree_info* info);
+panda_status panda_tree_copy(const panda_tree* tree, float* host_nodes, float* host_points);
+
+/* ---- diagnostics --------------------------------------------------------------
+ * Phase timing: when enabled, the library records CUDA events on the launching
+ * stream around each phase of the next builds/queries.  panda_phase_times
+ * writes up to `cap` (name, milliseconds, launches) triples of the last call
+ * that finished on this thread and returns how many there were. */
+void panda_set_phase_timing(int32_t enable);
+int32_t panda_phase_times(const char** names, float* ms, int32_t* launches, int32_t cap);
+/* Number of kernels this library launched on this thread so far. */
+int64_t panda_kernel_launches(void);
+
+const char* panda_status_string(panda_status status);
+const char* panda_last_error(void); /* thread-local; "" if none */
+const char* panda_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PANDA_H */

@@ -1,0 +1,407 @@
+// api.cu -- the C ABI declared in include/panda.h and the host runtime
+// (errors, launch accounting, phase timing, stream-ordered workspace).
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "runtime.h"
+
+namespace panda {
+
+namespace {
+thread_local char g_err[512] = "";
+thread_local int64_t g_launches = 0;
+bool g_timing = false;
+
+struct PhaseRow {
+    const char* name;
+    float ms;
+    int32_t launches;
+};
+thread_local std::vector<PhaseRow> g_phases;
+
+std::once_flag g_pool_once[64];
+int g_sms[64] = {0};
+}  // namespace
+
+void set_error(const char* fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+void clear_error() { g_err[0] = 0; }
+
+panda_status cuda_fail(cudaError_t e, const char* what)
+{
+    set_error("%s: %s (%s)", what, cudaGetErrorString(e), cudaGetErrorName(e));
+    cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? PANDA_ERR_OUT_OF_MEMORY : PANDA_ERR_CUDA;
+}
+
+panda_status note_launch(const char* what)
+{
+    g_launches++;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, what);
+    return PANDA_OK;
+}
+
+int64_t launches_so_far() { return g_launches; }
+bool phase_timing_enabled() { return g_timing; }
+
+PhaseTimer::PhaseTimer(cudaStream_t s) : stream_(s), on_(g_timing) {}
+
+PhaseTimer::~PhaseTimer()
+{
+    if (!on_) return;
+    for (int i = 0; i < n_ + (open_ ? 1 : 0) && i < 65; i++)
+        if (ev_[i]) cudaEventDestroy(ev_[i]);
+}
+
+void PhaseTimer::begin(const char* name)
+{
+    if (!on_) return;
+    if (n_ >= 64) return;
+    if (!open_) {
+        cudaEventCreate(&ev_[0]);
+        cudaEventRecord(ev_[0], stream_);
+        launches_at_[0] = g_launches;
+        open_ = true;
+    } else {
+        cudaEventCreate(&ev_[n_ + 1]);
+        cudaEventRecord(ev_[n_ + 1], stream_);
+        launches_at_[n_ + 1] = g_launches;
+        n_++;
+    }
+    names_[n_] = name;
+}
+
+void PhaseTimer::end()
+{
+    if (!on_ || !open_ || n_ >= 64) return;
+    cudaEventCreate(&ev_[n_ + 1]);
+    cudaEventRecord(ev_[n_ + 1], stream_);
+    launches_at_[n_ + 1] = g_launches;
+    n_++;
+    open_ = false;
+}
+
+void PhaseTimer::finish()
+{
+    if (!on_) return;
+    if (open_) end();
+    g_phases.clear();
+    if (n_ == 0) return;
+    cudaEventSynchronize(ev_[n_]);
+    for (int i = 0; i < n_; i++) {
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, ev_[i], ev_[i + 1]);
+        int32_t l = (int32_t)(launches_at_[i + 1] - launches_at_[i]);
+        bool merged = false;
+        for (auto& r : g_phases)
+            if (strcmp(r.name, names_[i]) == 0) {
+                r.ms += ms;
+                r.launches += l;
+                merged = true;
+                break;
+            }
+        if (!merged) g_phases.push_back({names_[i], ms, l});
+    }
+    open_ = false;
+}
+
+int num_sms()
+{
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) return 152;
+    if (!g_sms[dev]) {
+        int v = 0;
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+        g_sms[dev] = v > 0 ? v : 152;
+    }
+    return g_sms[dev];
+}
+
+panda_status ws_alloc(void** p, size_t bytes, cudaStream_t s, const char* what)
+{
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev >= 0 && dev < 64) {
+        std::call_once(g_pool_once[dev], [dev]() {
+            cudaMemPool_t pool;
+            if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+                uint64_t keep = UINT64_MAX;
+                cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+            }
+            cudaGetLastError();
+        });
+    }
+    *p = nullptr;
+    cudaError_t e = cudaMallocAsync(p, bytes, s);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        set_error("allocating %zu bytes for %s: %s", bytes, what, cudaGetErrorString(e));
+        cudaGetLastError();
+        return e == cudaErrorMemoryAllocation ? PANDA_ERR_OUT_OF_MEMORY : PANDA_ERR_CUDA;
+    }
+    return PANDA_OK;
+}
+
+void ws_free(void* p, cudaStream_t s)
+{
+    if (p) cudaFreeAsync(p, s);
+}
+
+bool is_device_ptr(const void* p)
+{
+    cudaPointerAttributes attr;
+    cudaError_t e = cudaPointerGetAttributes(&attr, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace panda
+
+using namespace panda;
+
+extern "C" {
+
+const char* panda_version(void) { return "panda-gb300 0.1 (sm_103a)"; }
+
+const char* panda_status_string(panda_status s)
+{
+    switch (s) {
+        case PANDA_OK: return "ok";
+        case PANDA_ERR_INVALID_ARGUMENT: return "invalid argument";
+        case PANDA_ERR_NONFINITE_INPUT: return "non-finite input";
+        case PANDA_ERR_UNSUPPORTED: return "unsupported";
+        case PANDA_ERR_OUT_OF_MEMORY: return "out of memory";
+        case PANDA_ERR_CUDA: return "cuda error";
+        case PANDA_ERR_TIMEOUT: return "timeout";
+        case PANDA_ERR_QUEUE_FULL: return "queue full";
+        case PANDA_ERR_DEPTH: return "depth limit exceeded";
+    }
+    return "unknown status";
+}
+
+const char* panda_last_error(void) { return g_err; }
+
+void panda_set_phase_timing(int32_t enable) { g_timing = enable != 0; }
+
+int32_t panda_phase_times(const char** names, float* ms, int32_t* launches, int32_t cap)
+{
+    int32_t n = (int32_t)g_phases.size();
+    for (int32_t i = 0; i < n && i < cap; i++) {
+        if (names) names[i] = g_phases[i].name;
+        if (ms) ms[i] = g_phases[i].ms;
+        if (launches) launches[i] = g_phases[i].launches;
+    }
+    return n;
+}
+
+int64_t panda_kernel_launches(void) { return g_launches; }
+
+panda_status panda_build_async(const float* points, int64_t n, int32_t d, int32_t bucket, void* stream,
+                               panda_tree** out)
+{
+    if (!out) {
+        set_error("panda_build: out is NULL");
+        return PANDA_ERR_INVALID_ARGUMENT;
+    }
+    clear_error();
+    try {
+        return build_tree(points, n, d, bucket, (cudaStream_t)stream, out);
+    } catch (...) {
+        set_error("panda_build: host exception");
+        return PANDA_ERR_OUT_OF_MEMORY;
+    }
+}
+
+panda_status panda_build(const float* points, int64_t n, int32_t d, int32_t bucket, panda_tree** out)
+{
+    panda_status s = panda_build_async(points, n, d, bucket, nullptr, out);
+    if (s == PANDA_OK) {
+        cudaError_t e = cudaStreamSynchronize(nullptr);
+        if (e != cudaSuccess) {
+            panda_free(*out);
+            *out = nullptr;
+            return cuda_fail(e, "panda_build");
+        }
+    }
+    return s;
+}
+
+panda_status panda_build_host(const float* points, int64_t n, int32_t d, int32_t bucket, void* stream,
+                              panda_tree** out)
+{
+    if (!out || !points || n < 1 || d < 1 || d > kMaxDim) {
+        if (out) *out = nullptr;
+        set_error("panda_build_host: invalid argument");
+        return (d > kMaxDim) ? PANDA_ERR_UNSUPPORTED : PANDA_ERR_INVALID_ARGUMENT;
+    }
+    clear_error();
+    cudaStream_t s = (cudaStream_t)stream;
+    void* dev = nullptr;
+    const size_t bytes = (size_t)n * d * sizeof(float);
+    panda_status st = ws_alloc(&dev, bytes, s, "host points staging");
+    if (st != PANDA_OK) return st;
+    cudaError_t e = cudaMemcpyAsync(dev, points, bytes, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) {
+        ws_free(dev, s);
+        return cuda_fail(e, "panda_build_host copy");
+    }
+    try {
+        st = build_tree(static_cast<const float*>(dev), n, d, bucket, s, out);
+    } catch (...) {
+        st = PANDA_ERR_OUT_OF_MEMORY;
+    }
+    ws_free(dev, s);
+    return st;
+}
+
+panda_status panda_knn_async(const panda_tree* tree, const float* queries, int64_t m, int32_t k,
+                             int32_t* out_ids, float* out_d2, const panda_query_params* params, void* stream)
+{
+    clear_error();
+    try {
+        return knn_query(tree, queries, m, k, out_ids, out_d2, params, (cudaStream_t)stream, nullptr);
+    } catch (...) {
+        set_error("panda_knn: host exception");
+        return PANDA_ERR_OUT_OF_MEMORY;
+    }
+}
+
+panda_status panda_knn(const panda_tree* tree, const float* queries, int64_t m, int32_t k, int32_t* out_ids,
+                       float* out_d2)
+{
+    clear_error();
+    unsigned herr = 0;
+    panda_status s;
+    try {
+        s = knn_query(tree, queries, m, k, out_ids, out_d2, nullptr, nullptr, &herr);
+    } catch (...) {
+        set_error("panda_knn: host exception");
+        return PANDA_ERR_OUT_OF_MEMORY;
+    }
+    if (s == PANDA_OK && (herr & kErrNonfinite)) {
+        set_error("panda_knn: non-finite query coordinate");
+        return PANDA_ERR_NONFINITE_INPUT;
+    }
+    if (s == PANDA_OK && herr) {
+        set_error("panda_knn: internal consistency check failed (0x%x)", herr);
+        return PANDA_ERR_CUDA;
+    }
+    return s;
+}
+
+panda_status panda_knn_host(const panda_tree* tree, const float* queries, int64_t m, int32_t k, int32_t* out_ids,
+                            float* out_d2, const panda_query_params* params, void* stream)
+{
+    clear_error();
+    if (!tree || m < 0 || k < 1 || (m > 0 && (!queries || !out_ids || !out_d2))) {
+        set_error("panda_knn_host: invalid argument");
+        return PANDA_ERR_INVALID_ARGUMENT;
+    }
+    if (k > kMaxK) {
+        set_error("panda_knn_host: k=%d above the maximum %d", k, kMaxK);
+        return PANDA_ERR_UNSUPPORTED;
+    }
+    if (m == 0) return PANDA_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    void *dq = nullptr, *di = nullptr, *dd = nullptr;
+    const size_t qb = (size_t)m * tree->d * sizeof(float), ob = (size_t)m * k * 4;
+    panda_status st = ws_alloc(&dq, qb, s, "query staging");
+    if (st == PANDA_OK) st = ws_alloc(&di, ob, s, "id staging");
+    if (st == PANDA_OK) st = ws_alloc(&dd, ob, s, "distance staging");
+    cudaError_t e = cudaSuccess;
+    unsigned herr = 0;
+    if (st == PANDA_OK) {
+        e = cudaMemcpyAsync(dq, queries, qb, cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) st = cuda_fail(e, "panda_knn_host copy in");
+    }
+    if (st == PANDA_OK) {
+        try {
+            st = knn_query(tree, static_cast<const float*>(dq), m, k, static_cast<int32_t*>(di),
+                           static_cast<float*>(dd), params, s, &herr);
+        } catch (...) {
+            st = PANDA_ERR_OUT_OF_MEMORY;
+        }
+    }
+    if (st == PANDA_OK) {
+        e = cudaMemcpyAsync(out_ids, di, ob, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(out_d2, dd, ob, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) st = cuda_fail(e, "panda_knn_host copy out");
+    }
+    ws_free(dq, s);
+    ws_free(di, s);
+    ws_free(dd, s);
+    if (st == PANDA_OK && (herr & kErrNonfinite)) {
+        set_error("panda_knn_host: non-finite query coordinate");
+        return PANDA_ERR_NONFINITE_INPUT;
+    }
+    return st;
+}
+
+void panda_free(panda_tree* tree)
+{
+    if (!tree) return;
+    int cur = 0;
+    cudaGetDevice(&cur);
+    if (cur != tree->device) cudaSetDevice(tree->device);
+    cudaDeviceSynchronize();
+    if (tree->nodes) cudaFree(tree->nodes);
+    if (tree->points) cudaFree(tree->points);
+    cudaGetLastError();
+    if (cur != tree->device) cudaSetDevice(cur);
+    delete tree;
+}
+
+panda_status panda_tree_get_info(const panda_tree* t, panda_tree_info* info)
+{
+    if (!t || !info) {
+        set_error("panda_tree_get_info: NULL argument");
+        return PANDA_ERR_INVALID_ARGUMENT;
+    }
+    info->n = t->n;
+    info->d = t->d;
+    info->bucket = t->bucket;
+    info->num_nodes = t->num_nodes;
+    info->num_leaves = t->num_leaves;
+    info->depth = t->depth;
+    info->node_floats = 4 * t->ns;
+    info->point_floats = 4 * t->nv;
+    info->subtree_threshold = t->threshold;
+    info->device_bytes = (int64_t)t->node_cap * t->ns * 16 + t->n * t->nv * 16;
+    return PANDA_OK;
+}
+
+panda_status panda_tree_copy(const panda_tree* t, float* host_nodes, float* host_points)
+{
+    if (!t) {
+        set_error("panda_tree_copy: NULL tree");
+        return PANDA_ERR_INVALID_ARGUMENT;
+    }
+    if (host_nodes)
+        PANDA_CUDA(cudaMemcpy(host_nodes, t->nodes, (size_t)t->num_nodes * t->ns * 16, cudaMemcpyDeviceToHost),
+                   "panda_tree_copy nodes");
+    if (host_points)
+        PANDA_CUDA(cudaMemcpy(host_points, t->points, (size_t)t->n * t->nv * 16, cudaMemcpyDeviceToHost),
+                   "panda_tree_copy points");
+    return PANDA_OK;
+}
+
+}  // extern "C"

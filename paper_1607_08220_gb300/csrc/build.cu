@@ -1,0 +1,1294 @@
+// build.cu -- kd-tree construction on GB300 (sm_103a).
+//
+// Method (arXiv 1607.08220): Sec. III-A steps ii-iv and Sec. III-A1.
+//   * Data-parallel levels (step ii): every node with more than T points is
+//     split by grid-wide passes, one level at a time: a 1024-point sample per
+//     node gives the split dimension (maximum sample variance) and the sorted
+//     "interval points"; a histogram of all node points over those interval
+//     points gives the split value closest to 50% (Sec. III-A1); a stable
+//     partition then scatters coordinates and ids to the other ping-pong
+//     buffer.  Points move as coalesced structure-of-arrays columns.
+//   * Subtree stage (step iii): every node of at most T points is finished by
+//     one warp in shared memory, depth-first, with the same split rule
+//     (with every point in the sample the rule is an exact selection).
+//   * Packing (step iv): leaves of at most B points are written contiguously
+//     as packed records (coordinates + id) in leaf order.
+// Every node stores its tight bounding box (level-stage boxes are the union of
+// their children's, computed bottom-up at the end).
+//
+// Split rule readings (identical in the CPU oracle, written independently):
+//   sample positions floor(j*n/S'), S' = min(1024, n); FP32 variance summed
+//   in 32 strided partials then a pairwise tree; argmax with ties to the lowest
+//   dimension; c_j = #{x < v_j}; j* = argmin |2c_j - n| (ties to the smallest
+//   j); left = x[dim] < s; duplicate fallback (next value above the node
+//   minimum) and index split for constant nodes.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "common.cuh"
+#include "runtime.h"
+
+namespace panda {
+
+struct BuildArgs {
+    int n, d, dp, bucket, T, n_pad;
+    const float* in;
+    float* X[2];
+    int* ID[2];
+    Active* act[2];
+    int act_cap;
+    int* tile_base[2];
+    Tile* tiles[2];
+    int tile_cap;
+    int* tleft;
+    int* tleftoff;
+    float* vs;
+    int* nhist;
+    float* nvar;
+    int* ndim;
+    int* nmode;
+    float* nsplit;
+    int* nleft;
+    int* nsel;
+    Small* small;
+    int small_cap;
+    int* lvl_nodes;
+    int* lvl_count;
+    int lvl_stride;
+    int* cnt;
+    unsigned* err;
+    float4* nodes;
+    long long node_cap;
+    int ns;
+    float4* pts;
+    int nv;
+};
+
+__device__ __forceinline__ bool finite_bits(float v)
+{
+    return (__float_as_uint(v) & 0x7f800000u) != 0x7f800000u;
+}
+
+// ------------------------------------------------------------------ A1
+
+__global__ void k_transpose(BuildArgs a)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    bool bad = false;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < a.n_pad; i += stride) {
+        if (i < a.n) {
+            for (int k = 0; k < a.d; k++) {
+                float v = a.in[i * a.d + k];
+                bad |= !finite_bits(v);
+                a.X[0][(long long)k * a.n_pad + i] = v;
+            }
+            a.ID[0][i] = (int)i;
+        } else {
+            for (int k = 0; k < a.d; k++) a.X[0][(long long)k * a.n_pad + i] = 0.0f;
+            a.ID[0][i] = -1;
+        }
+    }
+    if (bad) atomicOr(a.err, kErrNonfinite);
+}
+
+// ------------------------------------------------------------------ block helpers
+
+// Exclusive scan of one int per thread over the block (blockDim multiple of 32,
+// <= 1024).  Returns the exclusive prefix; *total gets the block sum.
+__device__ int block_excl_scan(int v, int* sh /*[33]*/, int* total)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    int incl = warp_incl_scan(v);
+    if (lane == 31) sh[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        int w = lane < nw ? sh[lane] : 0;
+        int wi = warp_incl_scan(w);
+        if (lane < nw) sh[lane] = wi - w;
+        if (lane == nw - 1) sh[32] = wi;
+    }
+    __syncthreads();
+    int r = sh[warp] + incl - v;
+    *total = sh[32];
+    __syncthreads();
+    return r;
+}
+
+// Tiles of the active list `x` (count A): node a covers [start, start+count),
+// cut at absolute multiples of kTile so that interior tiles are aligned.
+__device__ void block_plan_tiles(BuildArgs& a, int x, int A)
+{
+    __shared__ int sh[33];
+    __shared__ int base;
+    if (threadIdx.x == 0) base = 0;
+    __syncthreads();
+    for (int c = 0; c < A; c += blockDim.x) {
+        int ai = c + threadIdx.x;
+        int nt = 0;
+        Active nd;
+        if (ai < A) {
+            nd = a.act[x][ai];
+            int first = nd.start / kTile, last = (nd.start + nd.count - 1) / kTile;
+            nt = last - first + 1;
+        }
+        int tot;
+        int off = block_excl_scan(nt, sh, &tot) + base;
+        if (ai < A) {
+            a.tile_base[x][ai] = off;
+            int first = nd.start / kTile;
+            for (int j = 0; j < nt; j++) {
+                if (off + j >= a.tile_cap) { atomicOr(a.err, kErrTileOverflow); break; }
+                Tile t;
+                t.node = ai;
+                t.begin = max(nd.start, (first + j) * kTile);
+                t.end = min(nd.start + nd.count, (first + j + 1) * kTile);
+                t.first = (j == 0);
+                a.tiles[x][off + j] = t;
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) base += tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        a.tile_base[x][A] = base;
+        a.cnt[kCntTiles0 + x] = min(base, a.tile_cap);
+    }
+}
+
+__global__ void k_init(BuildArgs a)
+{
+    if (a.n > a.T) {
+        if (threadIdx.x == 0) {
+            Active r;
+            r.start = 0;
+            r.count = a.n;
+            r.node = 0;
+            r.depth = 0;
+            a.act[0][0] = r;
+            a.cnt[kCntActive0] = 1;
+            a.cnt[kCntNodes] = 1;
+        }
+        __syncthreads();
+        block_plan_tiles(a, 0, 1);
+    } else if (threadIdx.x == 0) {
+        Small s;
+        s.start = 0;
+        s.count = a.n;
+        s.node = 0;
+        s.depth_parity = 0;
+        a.small[0] = s;
+        a.cnt[kCntSmall] = 1;
+        a.cnt[kCntNodes] = 1;
+    }
+}
+
+// ------------------------------------------------------------------ A2 + A3
+
+// One block per active node: sample, per-dimension variance, split dimension,
+// bitonic sort of the sample along it.
+__global__ void k_sample(BuildArgs a, int L)
+{
+    extern __shared__ float S[];   // [d][kSamples]
+    __shared__ float var[kMaxDim];
+    __shared__ int sdim;
+    const int cur = L & 1;
+    const int ai = blockIdx.x;
+    if (ai >= a.cnt[kCntActive0 + cur]) return;
+    const Active nd = a.act[cur][ai];
+    const int cnt = nd.count;
+    const int sp = cnt < kSamples ? cnt : kSamples;
+    const float* X = a.X[cur];
+    for (int j = threadIdx.x; j < kSamples; j += blockDim.x) {
+        long long pos = nd.start + (long long)j * cnt / sp;
+        for (int k = 0; k < a.d; k++)
+            S[k * kSamples + j] = (j < sp) ? X[(long long)k * a.n_pad + pos] : INFINITY;
+    }
+    int* nh = a.nhist + (long long)ai * (kSamples + 1);
+    for (int b = threadIdx.x; b <= kSamples; b += blockDim.x) nh[b] = 0;
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int k = warp; k < a.d; k += nw) {
+        const float* col = S + k * kSamples;
+        float part = 0.0f;
+        for (int j = lane; j < sp; j += 32) part = __fadd_rn(part, col[j]);
+        float mean = __fdiv_rn(fixed_order_warp_total(part), (float)sp);
+        float p2 = 0.0f;
+        for (int j = lane; j < sp; j += 32) {
+            float c = __fsub_rn(col[j], mean);
+            p2 = __fadd_rn(p2, __fmul_rn(c, c));
+        }
+        float v = __fdiv_rn(fixed_order_warp_total(p2), (float)sp);
+        if (lane == 0) var[k] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int dm = argmax_dims(var, a.d, 0u);
+        sdim = dm;
+        a.ndim[ai] = dm;
+        a.nmode[ai] = (var[dm] > 0.0f) ? kModeValue : kModePending;
+        for (int k = 0; k < a.d; k++) a.nvar[ai * kMaxDim + k] = var[k];
+    }
+    __syncthreads();
+    const int dm = sdim;
+    if (!(var[dm] > 0.0f)) return;
+    float* v = S + dm * kSamples;
+    for (int size = 2; size <= kSamples; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int t = threadIdx.x; t < kSamples / 2; t += blockDim.x) {
+                int i = 2 * t - (t & (stride - 1));
+                int j = i + stride;
+                bool up = (i & size) == 0;
+                float x = v[i], y = v[j];
+                if ((x > y) == up) {
+                    v[i] = y;
+                    v[j] = x;
+                }
+            }
+            __syncthreads();
+        }
+    }
+    float* out = a.vs + (long long)ai * kSamples;
+    for (int j = threadIdx.x; j < kSamples; j += blockDim.x) out[j] = v[j];
+}
+
+// ------------------------------------------------------------------ A4
+
+// Histogram bin of x: #{v_j <= x} over the sorted interval points, found with
+// a two-level search (every 32nd interval point first, then the 32 within).
+__device__ __forceinline__ int hist_bin(const float* coarse, const float* fine, float x)
+{
+    int cb = count_le32(coarse, x);
+    if (cb == 0) return 0;
+    int blk = cb - 1;
+    return blk * 32 + count_le32(fine + blk * 33, x);
+}
+
+__global__ void k_hist(BuildArgs a, int L)
+{
+    __shared__ float fine[32 * 33];
+    __shared__ float coarse[32];
+    __shared__ int hist[kSamples + 1];
+    const int cur = L & 1;
+    const int t = blockIdx.x;
+    if (t >= a.cnt[kCntTiles0 + cur]) return;
+    const Tile tl = a.tiles[cur][t];
+    const int ai = tl.node;
+    if (a.nmode[ai] != kModeValue) return;
+    const int dm = a.ndim[ai];
+    const float* vs = a.vs + (long long)ai * kSamples;
+    for (int j = threadIdx.x; j < kSamples; j += blockDim.x) {
+        float v = vs[j];
+        fine[(j >> 5) * 33 + (j & 31)] = v;
+        if ((j & 31) == 0) coarse[j >> 5] = v;
+    }
+    for (int b = threadIdx.x; b <= kSamples; b += blockDim.x) hist[b] = 0;
+    __syncthreads();
+    const float* col = a.X[cur] + (long long)dm * a.n_pad;
+    for (int i4 = (tl.begin & ~3) + 4 * threadIdx.x; i4 < tl.end; i4 += 4 * blockDim.x) {
+        float4 x4 = *reinterpret_cast<const float4*>(col + i4);
+        float xs[4] = {x4.x, x4.y, x4.z, x4.w};
+#pragma unroll
+        for (int e = 0; e < 4; e++) {
+            int i = i4 + e;
+            if (i >= tl.begin && i < tl.end) atomicAdd(&hist[hist_bin(coarse, fine, xs[e])], 1);
+        }
+    }
+    __syncthreads();
+    int* nh = a.nhist + (long long)ai * (kSamples + 1);
+    for (int b = threadIdx.x; b <= kSamples; b += blockDim.x) {
+        int h = hist[b];
+        if (h) atomicAdd(&nh[b], h);
+    }
+}
+
+// ------------------------------------------------------------------ A5 (split select)
+
+__device__ float block_reduce_min(float v, float* sh)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    v = warp_min(v);
+    if (lane == 0) sh[warp] = v;
+    __syncthreads();
+    float r = INFINITY;
+    for (int w = 0; w < nw; w++) r = fminf(r, sh[w]);
+    __syncthreads();
+    return r;
+}
+__device__ float block_reduce_max(float v, float* sh)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    v = warp_max(v);
+    if (lane == 0) sh[warp] = v;
+    __syncthreads();
+    float r = -INFINITY;
+    for (int w = 0; w < nw; w++) r = fmaxf(r, sh[w]);
+    __syncthreads();
+    return r;
+}
+__device__ int block_reduce_sum(int v, int* sh)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    v = warp_sum(v);
+    if (lane == 0) sh[warp] = v;
+    __syncthreads();
+    int r = 0;
+    for (int w = 0; w < nw; w++) r += sh[w];
+    __syncthreads();
+    return r;
+}
+
+__global__ void k_select(BuildArgs a, int L)
+{
+    __shared__ int s_sel, s_left;
+    __shared__ float shf[32];
+    __shared__ int shi[32];
+    const int cur = L & 1;
+    const int ai = blockIdx.x;
+    if (ai >= a.cnt[kCntActive0 + cur]) return;
+    const Active nd = a.act[cur][ai];
+    const int cnt = nd.count;
+    const int sp = cnt < kSamples ? cnt : kSamples;
+    int mode = a.nmode[ai];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (mode == kModeValue) {
+        if (warp == 0) {
+            const int* nh = a.nhist + (long long)ai * (kSamples + 1);
+            int tot = 0;
+            for (int r = 0; r < 32; r++) {
+                int j = 32 * lane + r;
+                if (j < sp) tot += nh[j];
+            }
+            int c = warp_incl_scan(tot) - tot;
+            unsigned long long best = ~0ull;
+            int best_c = 0;
+            for (int r = 0; r < 32; r++) {
+                int j = 32 * lane + r;
+                if (j < sp) {
+                    c += nh[j];
+                    long long e = 2LL * c - cnt;
+                    if (e < 0) e = -e;
+                    unsigned long long key = ((unsigned long long)e << 11) | (unsigned)j;
+                    if (key < best) {
+                        best = key;
+                        best_c = c;
+                    }
+                }
+            }
+            unsigned long long wbest = best;
+#pragma unroll
+            for (int o = 16; o >= 1; o >>= 1) {
+                unsigned long long ob = __shfl_xor_sync(kFull, wbest, o);
+                wbest = ob < wbest ? ob : wbest;
+            }
+            int jstar = (int)(wbest & 2047ull);
+            int cstar = __shfl_sync(kFull, best_c, jstar >> 5);
+            if (lane == 0) {
+                s_sel = jstar;
+                s_left = cstar;
+            }
+        }
+        __syncthreads();
+        if (s_left > 0) {
+            if (threadIdx.x == 0) {
+                a.nsplit[ai] = a.vs[(long long)ai * kSamples + s_sel];
+                a.nleft[ai] = s_left;
+                a.nsel[ai] = s_sel;
+            }
+            return;
+        }
+        mode = kModePending;
+    }
+    // Duplicate fallback: first non-constant dim in descending-variance order,
+    // split just above its minimum; index split if every dim is constant.
+    const float* X = a.X[cur];
+    const float* var = a.nvar + ai * kMaxDim;
+    unsigned used = 0;
+    int fdim = -1;
+    float fsplit = 0.0f, min0 = 0.0f;
+    for (int r = 0; r < a.d; r++) {
+        int k = argmax_dims(var, a.d, used);
+        used |= 1u << k;
+        const float* col = X + (long long)k * a.n_pad + nd.start;
+        float mn = INFINITY, mx = -INFINITY;
+        for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+            float x = col[i];
+            mn = fminf(mn, x);
+            mx = fmaxf(mx, x);
+        }
+        mn = block_reduce_min(mn, shf);
+        mx = block_reduce_max(mx, shf);
+        if (k == 0) min0 = mn;
+        if (mx > mn) {
+            float nxt = INFINITY;
+            for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+                float x = col[i];
+                if (x > mn) nxt = fminf(nxt, x);
+            }
+            fsplit = block_reduce_min(nxt, shf);
+            fdim = k;
+            break;
+        }
+    }
+    int left;
+    if (fdim >= 0) {
+        const float* col = X + (long long)fdim * a.n_pad + nd.start;
+        int c = 0;
+        for (int i = threadIdx.x; i < cnt; i += blockDim.x) c += col[i] < fsplit;
+        left = block_reduce_sum(c, shi);
+        mode = kModeValue;
+    } else {
+        // every dim constant (all were visited): min0 is dim 0's value
+        left = (cnt + 1) >> 1;
+        mode = kModeIndex;
+        fdim = 0;
+        fsplit = min0;
+    }
+    if (threadIdx.x == 0) {
+        a.nmode[ai] = mode;
+        a.ndim[ai] = fdim;
+        a.nsplit[ai] = fsplit;
+        a.nleft[ai] = left;
+        a.nsel[ai] = -1;
+    }
+}
+
+// Per-tile count of left points for nodes that span several tiles.
+__global__ void k_tilecount(BuildArgs a, int L)
+{
+    const int cur = L & 1;
+    const int lane = threadIdx.x & 31;
+    const int t = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (t >= a.cnt[kCntTiles0 + cur]) return;
+    const Tile tl = a.tiles[cur][t];
+    const int ai = tl.node;
+    const Active nd = a.act[cur][ai];
+    const int ntiles = a.tile_base[cur][ai + 1] - a.tile_base[cur][ai];
+    int v;
+    if (ntiles == 1) {
+        v = a.nleft[ai];
+    } else if (a.nmode[ai] == kModeIndex) {
+        int half = (nd.count + 1) >> 1;
+        v = min(max(half - (tl.begin - nd.start), 0), tl.end - tl.begin);
+    } else {
+        const float s = a.nsplit[ai];
+        const float* col = a.X[cur] + (long long)a.ndim[ai] * a.n_pad;
+        int c = 0;
+        for (int i4 = (tl.begin & ~3) + 4 * lane; i4 < tl.end; i4 += 128) {
+            float4 x4 = *reinterpret_cast<const float4*>(col + i4);
+            c += (i4 >= tl.begin && i4 < tl.end && x4.x < s);
+            c += (i4 + 1 >= tl.begin && i4 + 1 < tl.end && x4.y < s);
+            c += (i4 + 2 >= tl.begin && i4 + 2 < tl.end && x4.z < s);
+            c += (i4 + 3 >= tl.begin && i4 + 3 < tl.end && x4.w < s);
+        }
+        v = warp_sum(c);
+    }
+    if (lane == 0) a.tleft[t] = v;
+}
+
+// One block: per-tile left offsets, children creation (next level or subtree
+// stage), node headers of this level, tile plan of the next level.
+__global__ void k_children(BuildArgs a, int L)
+{
+    __shared__ int sh[33];
+    __shared__ int s_next, s_small;
+    const int cur = L & 1, nxt = cur ^ 1;
+    const int A = a.cnt[kCntActive0 + cur];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int ai = warp; ai < A; ai += nw) {
+        const int tb = min(a.tile_base[cur][ai], a.tile_cap);
+        const int te = min(a.tile_base[cur][ai + 1], a.tile_cap);
+        int running = 0;
+        for (int j0 = tb; j0 < te; j0 += 32) {
+            int j = j0 + lane;
+            int v = j < te ? a.tleft[j] : 0;
+            int incl = warp_incl_scan(v);
+            if (j < te) a.tleftoff[j] = running + incl - v;
+            running += __shfl_sync(kFull, incl, 31);
+        }
+        if (lane == 0 && running != a.nleft[ai]) atomicOr(a.err, kErrInternal);
+    }
+    const int base_id = a.cnt[kCntNodes];
+    if (threadIdx.x == 0) {
+        s_next = 0;
+        s_small = a.cnt[kCntSmall];
+    }
+    __syncthreads();
+    for (int c0 = 0; c0 < A; c0 += blockDim.x) {
+        const int ai = c0 + threadIdx.x;
+        const bool valid = ai < A;
+        Active nd;
+        int cl = 0, cr = 0, la = 0, ra = 0;
+        if (valid) {
+            nd = a.act[cur][ai];
+            cl = a.nleft[ai];
+            cr = nd.count - cl;
+            la = cl > a.T;
+            ra = cr > a.T;
+        }
+        int ta, ts;
+        int pa = block_excl_scan(la + ra, sh, &ta);
+        int ps = block_excl_scan(valid ? 2 - la - ra : 0, sh, &ts);
+        if (valid) {
+            const int child = base_id + 2 * ai;
+            const int cdepth = nd.depth + 1;
+            const int nbase = s_next + pa, sbase = s_small + ps;
+            int ia = 0, is = 0;
+            for (int side = 0; side < 2; side++) {
+                const int cs = side ? nd.start + cl : nd.start;
+                const int cc = side ? cr : cl;
+                const bool act = side ? ra : la;
+                if (act) {
+                    if (cdepth >= kMaxDepth) atomicOr(a.err, kErrDepth);
+                    if (nbase + ia < a.act_cap) {
+                        Active c;
+                        c.start = cs;
+                        c.count = cc;
+                        c.node = child + side;
+                        c.depth = cdepth;
+                        a.act[nxt][nbase + ia] = c;
+                    } else {
+                        atomicOr(a.err, kErrActiveOverflow);
+                    }
+                    ia++;
+                } else {
+                    if (sbase + is < a.small_cap) {
+                        Small s;
+                        s.start = cs;
+                        s.count = cc;
+                        s.node = child + side;
+                        s.depth_parity = (cdepth << 1) | nxt;
+                        a.small[sbase + is] = s;
+                    } else {
+                        atomicOr(a.err, kErrSmallOverflow);
+                    }
+                    is++;
+                }
+            }
+            const int mode = a.nmode[ai];
+            if (nd.node < a.node_cap) {
+                unsigned meta = (unsigned)a.ndim[ai] | (mode == kModeIndex ? kMetaIndex : 0u);
+                int4 h = make_int4(child, 0, __float_as_int(a.nsplit[ai]), (int)meta);
+                reinterpret_cast<int4*>(a.nodes)[(long long)nd.node * a.ns] = h;
+            }
+            a.lvl_nodes[L * a.lvl_stride + ai] = nd.node;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            s_next += ta;
+            s_small += ts;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        a.cnt[kCntNodes] = base_id + 2 * A;
+        if (base_id + 2 * A > a.node_cap) atomicOr(a.err, kErrNodeOverflow);
+        a.cnt[kCntActive0 + nxt] = min(s_next, a.act_cap);
+        a.cnt[kCntSmall] = s_small;
+        a.lvl_count[L] = A;
+        if (A > 0) a.cnt[kCntLevels] = L + 1;
+    }
+    __syncthreads();
+    block_plan_tiles(a, nxt, min(s_next, a.act_cap));
+}
+
+// Stable partition of every tile: left (x[dim] < s, or the first half for an
+// index split) then right, scattered into the other ping-pong buffer.  Offsets
+// come from a warp-ballot / shuffle prefix scan within the block and from the
+// per-tile left counts across blocks.
+__global__ void k_partition(BuildArgs a, int L)
+{
+    __shared__ int sh[33];
+    const int cur = L & 1, nxt = cur ^ 1;
+    const int t = blockIdx.x;
+    if (t >= a.cnt[kCntTiles0 + cur]) return;
+    const Tile tl = a.tiles[cur][t];
+    const int ai = tl.node;
+    const Active nd = a.act[cur][ai];
+    const int mode = a.nmode[ai];
+    const int dim = a.ndim[ai];
+    const float s = a.nsplit[ai];
+    const int nleft = a.nleft[ai];
+    const int loff = a.tleftoff[t];
+    int lpos = nd.start + loff;
+    int rpos = nd.start + nleft + (tl.begin - nd.start - loff);
+    const int half = (nd.count + 1) >> 1;
+    const float* Xs = a.X[cur];
+    float* Xd = a.X[nxt];
+    const int* Is = a.ID[cur];
+    int* Id = a.ID[nxt];
+    const long long np = a.n_pad;
+    for (int c0 = tl.begin & ~3; c0 < tl.end; c0 += 4 * blockDim.x) {
+        const int i4 = c0 + 4 * threadIdx.x;
+        const bool in = i4 < tl.end;
+        bool valid[4], left[4];
+        float key[4] = {0.f, 0.f, 0.f, 0.f};
+        if (in) {
+            float4 x4 = *reinterpret_cast<const float4*>(Xs + dim * np + i4);
+            key[0] = x4.x;
+            key[1] = x4.y;
+            key[2] = x4.z;
+            key[3] = x4.w;
+        }
+        int nl = 0, nv = 0;
+#pragma unroll
+        for (int e = 0; e < 4; e++) {
+            int i = i4 + e;
+            valid[e] = in && i >= tl.begin && i < tl.end;
+            left[e] = valid[e] && (mode == kModeIndex ? (i - nd.start < half) : (key[e] < s));
+            nl += left[e];
+            nv += valid[e];
+        }
+        int tot;
+        int packed = block_excl_scan(nl | ((nv - nl) << 16), sh, &tot);
+        int pl = lpos + (packed & 0xffff), pr = rpos + (packed >> 16);
+        int dst[4];
+        bool bad = false;
+#pragma unroll
+        for (int e = 0; e < 4; e++) {
+            dst[e] = left[e] ? pl : pr;
+            pl += left[e];
+            pr += valid[e] && !left[e];
+            // a destination outside the node would mean inconsistent counts: never write it
+            if (valid[e] && (dst[e] < nd.start || dst[e] >= nd.start + nd.count)) {
+                valid[e] = false;
+                bad = true;
+            }
+        }
+        if (bad) atomicOr(a.err, kErrInternal);
+        if (in) {
+            for (int k = 0; k < a.d; k++) {
+                float4 v = *reinterpret_cast<const float4*>(Xs + k * np + i4);
+                float* o = Xd + k * np;
+                if (valid[0]) o[dst[0]] = v.x;
+                if (valid[1]) o[dst[1]] = v.y;
+                if (valid[2]) o[dst[2]] = v.z;
+                if (valid[3]) o[dst[3]] = v.w;
+            }
+            int4 id = *reinterpret_cast<const int4*>(Is + i4);
+            if (valid[0]) Id[dst[0]] = id.x;
+            if (valid[1]) Id[dst[1]] = id.y;
+            if (valid[2]) Id[dst[2]] = id.z;
+            if (valid[3]) Id[dst[3]] = id.w;
+        }
+        lpos += tot & 0xffff;
+        rpos += tot >> 16;
+    }
+}
+
+// ------------------------------------------------------------------ A6 + A7
+
+struct WarpMem {
+    float* sx;            // [d][T] coordinates
+    int* sid;             // [T] ids
+    unsigned short* ix[2];  // [T] local indices, ping-pong
+    int* rh;              // [256] radix histogram
+    float* box;           // [2][kMaxDim] lo, hi
+    float* var;           // [kMaxDim]
+    int4* stk;            // [kMaxDepth + 4]
+};
+
+__host__ __device__ __forceinline__ size_t warp_bytes(int d, int T)
+{
+    size_t b = (size_t)4 * d * T + 4 * (size_t)T + 2 * 2 * (size_t)T + 256 * 4 + 3 * kMaxDim * 4;
+    b = (b + 15) & ~(size_t)15;
+    return b + (kMaxDepth + 4) * sizeof(int4);
+}
+
+// Write node `node`'s record: header + box (lo, hi over dp slots, zero padded).
+__device__ void write_node(const BuildArgs& a, int node, int4 hdr, const float* box)
+{
+    const int lane = threadIdx.x & 31;
+    if (node >= a.node_cap) return;
+    float4* rec = a.nodes + (long long)node * a.ns;
+    if (lane == 0) {
+        reinterpret_cast<int4*>(rec)[0] = hdr;
+    } else if (lane < a.ns) {
+        float f[4];
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            int slot = 4 * lane + q - 4;   // 0..2dp-1 box slots
+            float v = 0.0f;
+            if (slot < a.dp) {
+                if (slot < a.d) v = box[slot];
+            } else if (slot < 2 * a.dp) {
+                int k = slot - a.dp;
+                if (k < a.d) v = box[kMaxDim + k];
+            }
+            f[q] = v;
+        }
+        rec[lane] = make_float4(f[0], f[1], f[2], f[3]);
+    }
+}
+
+__global__ void k_subtree(BuildArgs a, int wbytes)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int T = a.T, d = a.d;
+    unsigned char* base = smem + (size_t)warp * wbytes;
+    WarpMem w;
+    w.sx = reinterpret_cast<float*>(base);
+    w.sid = reinterpret_cast<int*>(w.sx + (size_t)d * T);
+    w.ix[0] = reinterpret_cast<unsigned short*>(w.sid + T);
+    w.ix[1] = w.ix[0] + T;
+    w.rh = reinterpret_cast<int*>(w.ix[1] + T);
+    w.box = reinterpret_cast<float*>(w.rh + 256);
+    w.var = w.box + 2 * kMaxDim;
+    {
+        size_t off = (size_t)((unsigned char*)(w.var + kMaxDim) - base);
+        off = (off + 15) & ~(size_t)15;
+        w.stk = reinterpret_cast<int4*>(base + off);
+    }
+    const int nsmall = min(a.cnt[kCntSmall], a.small_cap);
+    for (;;) {
+        int si = 0;
+        if (lane == 0) si = atomicAdd(&a.cnt[kCntSmallNext], 1);
+        si = __shfl_sync(kFull, si, 0);
+        if (si >= nsmall) break;
+        const Small sn = a.small[si];
+        const int start = sn.start, count = sn.count, par = sn.depth_parity & 1;
+        if (count < 1 || count > T || start < 0 || start + count > a.n) {
+            if (lane == 0) atomicOr(a.err, kErrInternal);
+            continue;
+        }
+        const float* Xs = a.X[par];
+        for (int k = 0; k < d; k++)
+            for (int i = lane; i < count; i += 32)
+                w.sx[k * T + i] = Xs[(long long)k * a.n_pad + start + i];
+        for (int i = lane; i < count; i += 32) {
+            w.sid[i] = a.ID[par][start + i];
+            w.ix[0][i] = (unsigned short)i;
+        }
+        int sp = 0;
+        if (lane == 0) w.stk[0] = make_int4(0, count, sn.node, sn.depth_parity >> 1);
+        sp = 1;
+        __syncwarp();
+        while (sp > 0) {
+            const int4 e = w.stk[--sp];
+            __syncwarp();
+            const int ls = e.x, lc = e.y, node = e.z;
+            const int depth = e.w & 0xffff, rel = e.w >> 16;
+            const unsigned short* ixc = w.ix[rel & 1];
+            unsigned short* ixn = w.ix[(rel + 1) & 1];
+            const bool leaf = lc <= a.bucket || depth >= kMaxDepth;
+            {
+                // box (and, for inner nodes, the sample variance: every point is a sample)
+                for (int k = 0; k < d; k++) {
+                    const float* col = w.sx + k * T;
+                    float part = 0.0f, mn = INFINITY, mx = -INFINITY;
+                    for (int j = lane; j < lc; j += 32) {
+                        float x = col[ixc[ls + j]];
+                        part = __fadd_rn(part, x);
+                        mn = fminf(mn, x);
+                        mx = fmaxf(mx, x);
+                    }
+                    mn = warp_min(mn);
+                    mx = warp_max(mx);
+                    float vk = 0.0f;
+                    if (!leaf) {
+                        float mean = __fdiv_rn(fixed_order_warp_total(part), (float)lc);
+                        float p2 = 0.0f;
+                        for (int j = lane; j < lc; j += 32) {
+                            float c = __fsub_rn(col[ixc[ls + j]], mean);
+                            p2 = __fadd_rn(p2, __fmul_rn(c, c));
+                        }
+                        vk = __fdiv_rn(fixed_order_warp_total(p2), (float)lc);
+                    }
+                    if (lane == 0) {
+                        w.box[k] = mn;
+                        w.box[kMaxDim + k] = mx;
+                        w.var[k] = vk;
+                    }
+                }
+                __syncwarp();
+            }
+            if (leaf) {
+                if (lc > a.bucket) atomicOr(a.err, kErrDepth);
+                const int pstart = start + ls;
+                write_node(a, node, make_int4(pstart, lc, 0, (int)kMetaLeaf), w.box);
+                for (int i = lane; i < lc; i += 32) {
+                    const int p = ixc[ls + i];
+                    float4* o = a.pts + (long long)(pstart + i) * a.nv;
+                    for (int v4 = 0; v4 < a.nv; v4++) {
+                        float f[4];
+#pragma unroll
+                        for (int q = 0; q < 4; q++) {
+                            int slot = 4 * v4 + q;
+                            float val = 0.0f;
+                            if (slot < d) val = w.sx[slot * T + p];
+                            else if (slot == a.dp) val = __int_as_float(w.sid[p]);
+                            f[q] = val;
+                        }
+                        o[v4] = make_float4(f[0], f[1], f[2], f[3]);
+                    }
+                }
+                if (lane == 0) {
+                    atomicAdd(&a.cnt[kCntLeaves], 1);
+                    atomicMax(&a.cnt[kCntDepth], depth);
+                }
+                __syncwarp();
+                continue;
+            }
+            // ---- split rule (S' = lc: exact selection form of the sampled rule)
+            int dim = argmax_dims(w.var, d, 0u);
+            int mode = -1, cleft = 0;
+            float s = 0.0f;
+            if (w.var[dim] > 0.0f) {
+                const float* col = w.sx + dim * T;
+                int rank = lc >> 1;
+                uint32_t prefix = 0, mask = 0;
+                for (int shift = 24; shift >= 0; shift -= 8) {
+                    for (int b = lane; b < 256; b += 32) w.rh[b] = 0;
+                    __syncwarp();
+                    for (int j = lane; j < lc; j += 32) {
+                        uint32_t key = float_key(col[ixc[ls + j]]);
+                        if ((key & mask) == prefix) atomicAdd(&w.rh[(key >> shift) & 255], 1);
+                    }
+                    __syncwarp();
+                    int loc = 0;
+#pragma unroll
+                    for (int q = 0; q < 8; q++) loc += w.rh[8 * lane + q];
+                    int incl = warp_incl_scan(loc);
+                    int excl = incl - loc;
+                    int found = -1, below = 0;
+                    if (rank >= excl && rank < incl) {
+                        int c = excl;
+                        for (int q = 0; q < 8; q++) {
+                            int h = w.rh[8 * lane + q];
+                            if (rank < c + h) {
+                                found = 8 * lane + q;
+                                below = c;
+                                break;
+                            }
+                            c += h;
+                        }
+                    }
+                    unsigned bal = __ballot_sync(kFull, found >= 0);
+                    int src = __ffs(bal) - 1;
+                    int digit = __shfl_sync(kFull, found, src);
+                    below = __shfl_sync(kFull, below, src);
+                    prefix |= (uint32_t)digit << shift;
+                    mask |= 0xffu << shift;
+                    rank -= below;
+                    __syncwarp();
+                }
+                const float vp = key_float(prefix);
+                int na = 0, nb = 0;
+                float up = INFINITY;
+                for (int j = lane; j < lc; j += 32) {
+                    float x = col[ixc[ls + j]];
+                    na += x < vp;
+                    nb += x <= vp;
+                    if (x > vp) up = fminf(up, x);
+                }
+                na = warp_sum(na);
+                nb = warp_sum(nb);
+                up = warp_min(up);
+                long long e1 = 2LL * na - lc;
+                if (e1 < 0) e1 = -e1;
+                float sv = vp;
+                int cv = na;
+                if (nb < lc) {
+                    long long e2 = 2LL * nb - lc;
+                    if (e2 < 0) e2 = -e2;
+                    if (e2 < e1) {
+                        sv = up;
+                        cv = nb;
+                    }
+                }
+                if (cv > 0) {
+                    mode = kModeValue;
+                    s = sv;
+                    cleft = cv;
+                }
+            }
+            if (mode < 0) {
+                unsigned used = 0;
+                for (int r = 0; r < d && mode < 0; r++) {
+                    int k = argmax_dims(w.var, d, used);
+                    used |= 1u << k;
+                    const float mn = w.box[k], mx = w.box[kMaxDim + k];
+                    if (mx > mn) {
+                        const float* col = w.sx + k * T;
+                        float nxt = INFINITY;
+                        for (int j = lane; j < lc; j += 32) {
+                            float x = col[ixc[ls + j]];
+                            if (x > mn) nxt = fminf(nxt, x);
+                        }
+                        nxt = warp_min(nxt);
+                        int c = 0;
+                        for (int j = lane; j < lc; j += 32) c += col[ixc[ls + j]] < nxt;
+                        cleft = warp_sum(c);
+                        s = nxt;
+                        dim = k;
+                        mode = kModeValue;
+                    }
+                }
+                if (mode < 0) {
+                    mode = kModeIndex;
+                    dim = 0;
+                    s = w.box[0];
+                    cleft = (lc + 1) >> 1;
+                }
+            }
+            // ---- stable partition by warp ballots
+            {
+                const float* col = w.sx + dim * T;
+                const int half = (lc + 1) >> 1;
+                int lcnt = 0, rcnt = 0;
+                for (int b0 = 0; b0 < lc; b0 += 32) {
+                    const int j = b0 + lane;
+                    const bool valid = j < lc;
+                    const int p = valid ? ixc[ls + j] : 0;
+                    const bool lft = valid && (mode == kModeIndex ? (j < half) : (col[p] < s));
+                    const unsigned bl = __ballot_sync(kFull, lft);
+                    const unsigned bv = __ballot_sync(kFull, valid);
+                    const unsigned br = bv & ~bl;
+                    if (lft) ixn[ls + lcnt + __popc(bl & lanemask_lt())] = (unsigned short)p;
+                    else if (valid) ixn[ls + cleft + rcnt + __popc(br & lanemask_lt())] = (unsigned short)p;
+                    lcnt += __popc(bl);
+                    rcnt += __popc(br);
+                }
+                if (lane == 0 && lcnt != cleft) atomicOr(a.err, kErrInternal);
+            }
+            int c0 = 0;
+            if (lane == 0) c0 = atomicAdd(&a.cnt[kCntNodes], 2);
+            c0 = __shfl_sync(kFull, c0, 0);
+            if (c0 + 2 > a.node_cap && lane == 0) atomicOr(a.err, kErrNodeOverflow);
+            unsigned meta = (unsigned)dim | (mode == kModeIndex ? kMetaIndex : 0u);
+            write_node(a, node, make_int4(c0, 0, __float_as_int(s), (int)meta), w.box);
+            __syncwarp();
+            if (lane == 0) {
+                const int ew = (depth + 1) | ((rel + 1) << 16);
+                w.stk[sp] = make_int4(ls + cleft, lc - cleft, c0 + 1, ew);
+                w.stk[sp + 1] = make_int4(ls, cleft, c0, ew);
+            }
+            sp += 2;
+            __syncwarp();
+        }
+    }
+}
+
+// Bottom-up boxes of the level-stage nodes: union of the two children.
+__global__ void k_boxes(BuildArgs a, int nlevels)
+{
+    for (int L = nlevels - 1; L >= 0; L--) {
+        const int A = a.lvl_count[L];
+        for (int i = threadIdx.x; i < A; i += blockDim.x) {
+            const int node = a.lvl_nodes[L * a.lvl_stride + i];
+            if (node >= a.node_cap) continue;
+            float* rec = reinterpret_cast<float*>(a.nodes + (long long)node * a.ns);
+            const int c = reinterpret_cast<const int*>(rec)[0];
+            if (c + 1 >= a.node_cap) continue;
+            const float* r0 = reinterpret_cast<const float*>(a.nodes + (long long)c * a.ns);
+            const float* r1 = reinterpret_cast<const float*>(a.nodes + (long long)(c + 1) * a.ns);
+            for (int k = 0; k < a.d; k++) {
+                rec[4 + k] = fminf(r0[4 + k], r1[4 + k]);
+                rec[4 + a.dp + k] = fmaxf(r0[4 + a.dp + k], r1[4 + a.dp + k]);
+            }
+            for (int k = a.d; k < a.dp; k++) {
+                rec[4 + k] = 0.0f;
+                rec[4 + a.dp + k] = 0.0f;
+            }
+            for (int q = 4 + 2 * a.dp; q < 4 * a.ns; q++) rec[q] = 0.0f;
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------ host
+
+namespace {
+
+struct Buffers {
+    std::vector<void*> ptrs;
+    cudaStream_t s;
+    explicit Buffers(cudaStream_t st) : s(st) {}
+    ~Buffers() { for (void* p : ptrs) ws_free(p, s); }
+    template <typename T>
+    panda_status get(T** out, size_t count, const char* what)
+    {
+        void* p = nullptr;
+        panda_status st = ws_alloc(&p, std::max<size_t>(count, 1) * sizeof(T), s, what);
+        if (st != PANDA_OK) return st;
+        ptrs.push_back(p);
+        *out = static_cast<T*>(p);
+        return PANDA_OK;
+    }
+};
+
+int subtree_threshold(int d, int bucket)
+{
+    (void)d;
+    int T = 1024;
+    return std::max(T, bucket);
+}
+
+panda_status configure_kernels()
+{
+    static bool done = false;
+    if (done) return PANDA_OK;
+    PANDA_CUDA(cudaFuncSetAttribute(k_sample, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    kMaxDim * kSamples * 4),
+               "configure k_sample");
+    PANDA_CUDA(cudaFuncSetAttribute(k_subtree, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024),
+               "configure k_subtree");
+    done = true;
+    return PANDA_OK;
+}
+
+struct Plan {
+    int T, act_cap, tile_cap, small_cap, lvl_stride, max_levels;
+    long long node_cap;
+};
+
+panda_status build_once(const float* points, int n, int d, int bucket, cudaStream_t stream,
+                        const Plan& pl, panda_tree* t, int* need_small, long long* need_nodes,
+                        unsigned* err_out)
+{
+    PhaseTimer timer(stream);
+    Buffers ws(stream);
+    BuildArgs a;
+    memset(&a, 0, sizeof(a));
+    a.n = n;
+    a.d = d;
+    a.dp = t->dp;
+    a.bucket = bucket;
+    a.T = pl.T;
+    a.n_pad = (n + 3) & ~3;
+    a.in = points;
+    a.act_cap = pl.act_cap;
+    a.tile_cap = pl.tile_cap;
+    a.small_cap = pl.small_cap;
+    a.lvl_stride = pl.lvl_stride;
+    a.node_cap = pl.node_cap;
+    a.ns = t->ns;
+    a.nv = t->nv;
+    a.nodes = t->nodes;
+    a.pts = t->points;
+    panda_status st;
+#define GET(ptr, count, what) \
+    if ((st = ws.get(&(ptr), (count), what)) != PANDA_OK) return st
+    const size_t np = (size_t)a.n_pad;
+    for (int p = 0; p < 2; p++) {
+        GET(a.X[p], np * d, "coordinate buffers");
+        GET(a.ID[p], np, "id buffers");
+        GET(a.act[p], (size_t)pl.act_cap, "level lists");
+        GET(a.tile_base[p], (size_t)pl.act_cap + 1, "tile bases");
+        GET(a.tiles[p], (size_t)pl.tile_cap, "tiles");
+    }
+    GET(a.tleft, (size_t)pl.tile_cap, "tile counts");
+    GET(a.tleftoff, (size_t)pl.tile_cap, "tile offsets");
+    GET(a.vs, (size_t)pl.act_cap * kSamples, "samples");
+    GET(a.nhist, (size_t)pl.act_cap * (kSamples + 1), "histograms");
+    GET(a.nvar, (size_t)pl.act_cap * kMaxDim, "variances");
+    GET(a.ndim, (size_t)pl.act_cap, "split dims");
+    GET(a.nmode, (size_t)pl.act_cap, "split modes");
+    GET(a.nsplit, (size_t)pl.act_cap, "split values");
+    GET(a.nleft, (size_t)pl.act_cap, "left counts");
+    GET(a.nsel, (size_t)pl.act_cap, "split positions");
+    GET(a.small, (size_t)pl.small_cap, "subtree list");
+    GET(a.lvl_nodes, (size_t)pl.lvl_stride * pl.max_levels, "level nodes");
+    GET(a.lvl_count, (size_t)pl.max_levels, "level counts");
+    GET(a.cnt, (size_t)kCntSlots, "counters");
+    GET(a.err, (size_t)1, "error word");
+#undef GET
+    PANDA_CUDA(cudaMemsetAsync(a.cnt, 0, kCntSlots * sizeof(int), stream), "clear counters");
+    PANDA_CUDA(cudaMemsetAsync(a.err, 0, sizeof(unsigned), stream), "clear error word");
+    PANDA_CUDA(cudaMemsetAsync(a.lvl_count, 0, pl.max_levels * sizeof(int), stream), "clear levels");
+
+    const int sms = num_sms();
+    timer.begin("transpose");
+    {
+        int blocks = (int)std::min<long long>((a.n_pad + 255) / 256, (long long)sms * 16);
+        k_transpose<<<blocks, 256, 0, stream>>>(a);
+        PANDA_LAUNCHED("k_transpose");
+        k_init<<<1, 1024, 0, stream>>>(a);
+        PANDA_LAUNCHED("k_init");
+    }
+    auto launch_level = [&](int L) -> panda_status {
+        const int acap = (int)std::min<long long>(L < 30 ? (1LL << L) : (1LL << 30), pl.act_cap);
+        const int tcap = (int)std::min<long long>(pl.tile_cap, (long long)n / kTile + 2LL * acap + 2);
+        timer.begin("level.sample");
+        k_sample<<<acap, 256, d * kSamples * 4, stream>>>(a, L);
+        PANDA_LAUNCHED("k_sample");
+        timer.begin("level.hist");
+        k_hist<<<tcap, 256, 0, stream>>>(a, L);
+        PANDA_LAUNCHED("k_hist");
+        timer.begin("level.select");
+        k_select<<<acap, 256, 0, stream>>>(a, L);
+        PANDA_LAUNCHED("k_select");
+        k_tilecount<<<(tcap + 7) / 8, 256, 0, stream>>>(a, L);
+        PANDA_LAUNCHED("k_tilecount");
+        k_children<<<1, 1024, 0, stream>>>(a, L);
+        PANDA_LAUNCHED("k_children");
+        timer.begin("level.partition");
+        k_partition<<<tcap, 256, 0, stream>>>(a, L);
+        PANDA_LAUNCHED("k_partition");
+        return PANDA_OK;
+    };
+    int L = 0;
+    int levels_est = 0;
+    if (n > pl.T) {
+        double r = (double)n / pl.T;
+        levels_est = (int)ceil(log2(r)) + 2;
+    }
+    levels_est = std::min(levels_est, pl.max_levels);
+    for (; L < levels_est; L++)
+        if ((st = launch_level(L)) != PANDA_OK) return st;
+    int hc[kCntSlots];
+    unsigned herr = 0;
+    for (;;) {
+        PANDA_CUDA(cudaMemcpyAsync(hc, a.cnt, sizeof(hc), cudaMemcpyDeviceToHost, stream), "read counters");
+        PANDA_CUDA(cudaMemcpyAsync(&herr, a.err, sizeof(herr), cudaMemcpyDeviceToHost, stream), "read error");
+        PANDA_CUDA(cudaStreamSynchronize(stream), "level stage");
+        if (herr) break;
+        if (hc[kCntActive0 + (L & 1)] == 0) break;
+        if (L >= pl.max_levels) {
+            herr |= kErrDepth;
+            break;
+        }
+        if ((st = launch_level(L)) != PANDA_OK) return st;
+        L++;
+    }
+    *need_small = hc[kCntSmall];
+    *err_out = herr;
+    if (herr) return PANDA_OK;   // caller decides (retry or error)
+    const int nlevels = hc[kCntLevels];
+
+    timer.begin("subtree");
+    {
+        const int wb = (int)warp_bytes(d, pl.T);
+        int wpb = std::max(1, std::min(8, (227 * 1024) / wb));
+        k_subtree<<<sms, wpb * 32, (size_t)wpb * wb, stream>>>(a, wb);
+        PANDA_LAUNCHED("k_subtree");
+    }
+    timer.begin("boxes");
+    if (nlevels > 0) {
+        k_boxes<<<1, 1024, 0, stream>>>(a, nlevels);
+        PANDA_LAUNCHED("k_boxes");
+    }
+    timer.end();
+    PANDA_CUDA(cudaMemcpyAsync(hc, a.cnt, sizeof(hc), cudaMemcpyDeviceToHost, stream), "read counters");
+    PANDA_CUDA(cudaMemcpyAsync(&herr, a.err, sizeof(herr), cudaMemcpyDeviceToHost, stream), "read error");
+    PANDA_CUDA(cudaStreamSynchronize(stream), "subtree stage");
+    timer.finish();
+    *need_nodes = hc[kCntNodes];
+    *err_out = herr;
+    t->num_nodes = hc[kCntNodes];
+    t->num_leaves = hc[kCntLeaves];
+    t->depth = hc[kCntDepth];
+    return PANDA_OK;
+}
+
+}  // namespace
+
+panda_status build_tree(const float* points, int64_t n64, int32_t d, int32_t bucket, cudaStream_t stream,
+                        panda_tree** out)
+{
+    *out = nullptr;
+    if (!points || n64 < 1 || n64 >= (1LL << 31) - 4 || d < 1 || bucket < 1) {
+        set_error("panda_build: invalid argument (n=%lld d=%d bucket=%d)", (long long)n64, d, bucket);
+        return PANDA_ERR_INVALID_ARGUMENT;
+    }
+    if (d > kMaxDim || bucket > kMaxBucket) {
+        set_error("panda_build: unsupported d=%d or bucket=%d (max %d, %d)", d, bucket, kMaxDim, kMaxBucket);
+        return PANDA_ERR_UNSUPPORTED;
+    }
+    if (!is_device_ptr(points)) {
+        set_error("panda_build: points must be a device pointer");
+        return PANDA_ERR_INVALID_ARGUMENT;
+    }
+    panda_status st = configure_kernels();
+    if (st != PANDA_OK) return st;
+    const int n = (int)n64;
+    panda_tree* t = new panda_tree();
+    cudaGetDevice(&t->device);
+    t->n = n;
+    t->d = d;
+    t->dp = padded_dim(d);
+    t->bucket = bucket;
+    t->nv = point_float4s(t->dp);
+    t->ns = node_float4s(t->dp);
+    Plan pl;
+    pl.T = subtree_threshold(d, bucket);
+    t->threshold = pl.T;
+    pl.act_cap = n / (pl.T + 1) + 1;
+    pl.tile_cap = n / kTile + 2 * pl.act_cap + 4;
+    pl.small_cap = 4 * pl.act_cap + 16;
+    pl.lvl_stride = pl.act_cap;
+    pl.max_levels = kMaxDepth + 1;
+    pl.node_cap = 4LL * n / bucket + 8LL * pl.act_cap + 1024;
+    pl.node_cap = std::min<long long>(pl.node_cap, 2LL * n + 8);
+    for (int attempt = 0; attempt < 3; attempt++) {
+        t->node_cap = pl.node_cap;
+        void* pn = nullptr;
+        void* pp = nullptr;
+        st = ws_alloc(&pn, (size_t)pl.node_cap * t->ns * sizeof(float4), stream, "tree nodes");
+        if (st != PANDA_OK) break;
+        st = ws_alloc(&pp, (size_t)n * t->nv * sizeof(float4), stream, "tree points");
+        if (st != PANDA_OK) {
+            ws_free(pn, stream);
+            break;
+        }
+        t->nodes = static_cast<float4*>(pn);
+        t->points = static_cast<float4*>(pp);
+        int need_small = 0;
+        long long need_nodes = 0;
+        unsigned err = 0;
+        st = build_once(points, n, d, bucket, stream, pl, t, &need_small, &need_nodes, &err);
+        bool retry = false;
+        if (st == PANDA_OK && err) {
+            if (err & kErrNonfinite) {
+                set_error("panda_build: non-finite coordinate in the input");
+                st = PANDA_ERR_NONFINITE_INPUT;
+            } else if (err & kErrDepth) {
+                set_error("panda_build: a node below depth %d still holds more than %d points", kMaxDepth, bucket);
+                st = PANDA_ERR_DEPTH;
+            } else if (err & (kErrInternal | kErrTileOverflow | kErrActiveOverflow)) {
+                set_error("panda_build: internal consistency check failed (0x%x)", err);
+                st = PANDA_ERR_CUDA;
+            } else {
+                if (err & kErrSmallOverflow) pl.small_cap = std::max(pl.small_cap * 2, need_small + 16);
+                if (err & kErrNodeOverflow) pl.node_cap = std::min<long long>(2LL * n + 8, std::max(pl.node_cap * 2, need_nodes + 16));
+                retry = true;
+            }
+        }
+        if (st != PANDA_OK || retry) {
+            cudaStreamSynchronize(stream);
+            ws_free(t->nodes, stream);
+            ws_free(t->points, stream);
+            t->nodes = nullptr;
+            t->points = nullptr;
+            if (st != PANDA_OK) break;
+            continue;
+        }
+        // root box for query ordering
+        float rec[4 + 2 * kMaxDim + 4];
+        cudaError_t e = cudaMemcpyAsync(rec, t->nodes, t->ns * sizeof(float4), cudaMemcpyDeviceToHost, stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+        if (e != cudaSuccess) {
+            st = cuda_fail(e, "read root");
+            break;
+        }
+        for (int k = 0; k < d; k++) {
+            t->root_lo[k] = rec[4 + k];
+            t->root_hi[k] = rec[4 + t->dp + k];
+        }
+        *out = t;
+        return PANDA_OK;
+    }
+    if (st == PANDA_OK) {
+        set_error("panda_build: capacity retries exhausted");
+        st = PANDA_ERR_OUT_OF_MEMORY;
+    }
+    delete t;
+    return st;
+}
+
+}  // namespace panda

@@ -1,0 +1,308 @@
+// query.cu -- KNN query host path: query ordering and traversal dispatch.
+//
+// Algorithm 1 is run for many queries at once (the paper parallelises over
+// queries, Sec. V-B2).  To make the 32 queries of a warp traverse nearly the
+// same nodes, queries are first grouped by a spatial key with one counting
+// sort: either the leaf bucket the query falls into (descending the tree by
+// its split planes) or a 30-bit Morton code over the tree's root box.  The
+// order only changes which queries share a warp, never a result.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "common.cuh"
+#include "query.cuh"
+#include "runtime.h"
+
+namespace panda {
+
+struct OrderArgs {
+    const float4* nodes;
+    long long num_nodes;
+    const float* queries;
+    long long m;
+    int d, ns, shift, mode;
+    float lo[kMaxDim], inv[kMaxDim];
+    int bits;
+    unsigned* keys;
+    int* hist;
+};
+
+__device__ __forceinline__ unsigned morton_key(const OrderArgs& a, const float* q)
+{
+    unsigned code = 0;
+    unsigned cell[kMaxDim];
+    const unsigned top = (1u << a.bits) - 1u;
+    for (int k = 0; k < a.d; k++) {
+        float u = (q[k] - a.lo[k]) * a.inv[k];
+        u = fminf(fmaxf(u, 0.0f), 1.0f);
+        unsigned c = (unsigned)(u * (float)top);
+        cell[k] = c > top ? top : c;
+    }
+    for (int b = a.bits - 1; b >= 0; b--)
+        for (int k = 0; k < a.d; k++) code = (code << 1) | ((cell[k] >> b) & 1u);
+    return code;
+}
+
+__global__ void k_order_keys(OrderArgs a)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.m) return;
+    const float* q = a.queries + i * a.d;
+    unsigned key;
+    if (a.mode == PANDA_ORDER_MORTON) {
+        key = morton_key(a, q) >> a.shift;
+    } else {
+        int node = 0;
+        for (int step = 0; step <= kMaxDepth + 1; step++) {
+            if ((unsigned)node >= (unsigned)a.num_nodes) {
+                node = 0;
+                break;
+            }
+            const int4 h = __ldg(reinterpret_cast<const int4*>(a.nodes + (long long)node * a.ns));
+            const unsigned meta = (unsigned)h.w;
+            if (meta & kMetaLeaf) break;
+            if (meta & kMetaIndex) {
+                node = h.x;
+            } else {
+                const float s = __int_as_float(h.z);
+                node = h.x + (q[meta & kMetaDimMask] >= s ? 1 : 0);
+            }
+        }
+        const int4 h = __ldg(reinterpret_cast<const int4*>(a.nodes + (long long)node * a.ns));
+        key = (unsigned)h.x >> a.shift;
+    }
+    a.keys[i] = key;
+    atomicAdd(&a.hist[key], 1);
+}
+
+// Exclusive scan of hist[0..nb) in blocks of 4096; block sums to bsum.
+__global__ void k_scan_blocks(int* hist, int nb, int* bsum)
+{
+    __shared__ int sh[33];
+    const int base = blockIdx.x * 4096 + threadIdx.x * 4;
+    int v[4], t = 0;
+#pragma unroll
+    for (int e = 0; e < 4; e++) {
+        v[e] = base + e < nb ? hist[base + e] : 0;
+        t += v[e];
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int incl = warp_incl_scan(t);
+    if (lane == 31) sh[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        int w = sh[lane];
+        int wi = warp_incl_scan(w);
+        sh[lane] = wi - w;
+        if (lane == 31) sh[32] = wi;
+    }
+    __syncthreads();
+    int run = sh[warp] + incl - t;
+#pragma unroll
+    for (int e = 0; e < 4; e++) {
+        if (base + e < nb) hist[base + e] = run;
+        run += v[e];
+    }
+    if (threadIdx.x == 0) bsum[blockIdx.x] = sh[32];
+}
+
+__global__ void k_scan_sums(int* bsum, int nblocks)
+{
+    __shared__ int sh[33];
+    __shared__ int carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int c0 = 0; c0 < nblocks; c0 += blockDim.x) {
+        const int i = c0 + threadIdx.x;
+        const int v = i < nblocks ? bsum[i] : 0;
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        int incl = warp_incl_scan(v);
+        if (lane == 31) sh[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            int w = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0;
+            int wi = warp_incl_scan(w);
+            sh[lane] = wi - w;
+            if (lane == 31) sh[32] = wi;
+        }
+        __syncthreads();
+        if (i < nblocks) bsum[i] = carry + sh[warp] + incl - v;
+        __syncthreads();
+        if (threadIdx.x == 0) carry += sh[32];
+        __syncthreads();
+    }
+}
+
+__global__ void k_order_scatter(const unsigned* keys, long long m, int* cursor, const int* bsum, int* perm)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    const unsigned key = keys[i];
+    const int p = atomicAdd(&cursor[key], 1) + bsum[key >> 12];
+    perm[p] = (int)i;
+}
+
+template <int DP, int KC>
+static panda_status launch_knn_t(const KnnArgs& a, cudaStream_t s)
+{
+    const long long warps = (a.m + 31) / 32;
+    const long long blocks = (warps + 3) / 4;
+    k_knn<DP, KC><<<(unsigned)blocks, 128, 0, s>>>(a);
+    PANDA_LAUNCHED("k_knn");
+    return PANDA_OK;
+}
+
+template <int DP>
+static panda_status launch_knn_dp(const KnnArgs& a, int kc, cudaStream_t s)
+{
+    switch (kc) {
+        case 8: return launch_knn_t<DP, 8>(a, s);
+        case 16: return launch_knn_t<DP, 16>(a, s);
+        case 32: return launch_knn_t<DP, 32>(a, s);
+        default: return launch_knn_t<DP, 64>(a, s);
+    }
+}
+
+static panda_status launch_knn(const KnnArgs& a, int dp, int kc, cudaStream_t s)
+{
+    switch (dp) {
+        case 2: return launch_knn_dp<2>(a, kc, s);
+        case 3: return launch_knn_dp<3>(a, kc, s);
+        case 4: return launch_knn_dp<4>(a, kc, s);
+        case 8: return launch_knn_dp<8>(a, kc, s);
+        case 10: return launch_knn_dp<10>(a, kc, s);
+        default: return launch_knn_dp<16>(a, kc, s);
+    }
+}
+
+static int k_class(int k)
+{
+    if (k <= 8) return 8;
+    if (k <= 16) return 16;
+    if (k <= 32) return 32;
+    return 64;
+}
+
+panda_status knn_query(const panda_tree* t, const float* queries, int64_t m, int32_t k, int32_t* ids,
+                       float* d2, const panda_query_params* params, cudaStream_t stream,
+                       unsigned* host_err)
+{
+    if (host_err) *host_err = 0;
+    if (!t || m < 0 || k < 1 || (m > 0 && (!queries || !ids || !d2))) {
+        set_error("panda_knn: invalid argument");
+        return PANDA_ERR_INVALID_ARGUMENT;
+    }
+    if (k > kMaxK) {
+        set_error("panda_knn: k=%d above the maximum %d", k, kMaxK);
+        return PANDA_ERR_UNSUPPORTED;
+    }
+    if (m >= (1LL << 31)) {
+        set_error("panda_knn: m=%lld too large", (long long)m);
+        return PANDA_ERR_INVALID_ARGUMENT;
+    }
+    if (m == 0) return PANDA_OK;
+    if (!is_device_ptr(queries) || !is_device_ptr(ids) || !is_device_ptr(d2)) {
+        set_error("panda_knn: queries and outputs must be device pointers");
+        return PANDA_ERR_INVALID_ARGUMENT;
+    }
+    const int order = params ? params->order : PANDA_ORDER_LEAF;
+    if (order < PANDA_ORDER_NONE || order > PANDA_ORDER_LEAF) {
+        set_error("panda_knn: unknown order %d", order);
+        return PANDA_ERR_INVALID_ARGUMENT;
+    }
+    PhaseTimer timer(stream);
+    std::vector<void*> ws;
+    auto cleanup = [&]() {
+        for (void* p : ws) ws_free(p, stream);
+    };
+    panda_status st;
+    auto get = [&](void** p, size_t bytes, const char* what) -> panda_status {
+        panda_status r = ws_alloc(p, bytes, stream, what);
+        if (r == PANDA_OK) ws.push_back(*p);
+        return r;
+    };
+    unsigned* err = nullptr;
+    if ((st = get((void**)&err, sizeof(unsigned), "query error word")) != PANDA_OK) return cleanup(), st;
+    cudaError_t ce = cudaMemsetAsync(err, 0, sizeof(unsigned), stream);
+    if (ce != cudaSuccess) return cleanup(), cuda_fail(ce, "clear query error");
+    int* perm = nullptr;
+    if (order != PANDA_ORDER_NONE && m > 32) {
+        timer.begin("query.order");
+        OrderArgs oa;
+        memset(&oa, 0, sizeof(oa));
+        oa.nodes = t->nodes;
+        oa.num_nodes = t->num_nodes;
+        oa.queries = queries;
+        oa.m = m;
+        oa.d = t->d;
+        oa.ns = t->ns;
+        oa.mode = order;
+        int nb;
+        if (order == PANDA_ORDER_MORTON) {
+            oa.bits = std::max(1, std::min(10, 30 / t->d));
+            const int total = oa.bits * t->d;
+            oa.shift = std::max(0, total - 20);
+            nb = 1 << (total - oa.shift);
+            for (int j = 0; j < t->d; j++) {
+                oa.lo[j] = t->root_lo[j];
+                float w = t->root_hi[j] - t->root_lo[j];
+                oa.inv[j] = w > 0.0f ? 1.0f / w : 0.0f;
+            }
+        } else {
+            int sh = 0;
+            while (((long long)t->n >> sh) > (1 << 22)) sh++;
+            oa.shift = sh;
+            nb = (int)(((long long)t->n >> sh) + 1);
+        }
+        const int nblk = (nb + 4095) / 4096;
+        unsigned* keys = nullptr;
+        int *hist = nullptr, *bsum = nullptr;
+        if ((st = get((void**)&keys, (size_t)m * 4, "order keys")) != PANDA_OK) return cleanup(), st;
+        if ((st = get((void**)&perm, (size_t)m * 4, "order permutation")) != PANDA_OK) return cleanup(), st;
+        if ((st = get((void**)&hist, (size_t)nblk * 4096 * 4, "order histogram")) != PANDA_OK) return cleanup(), st;
+        if ((st = get((void**)&bsum, (size_t)nblk * 4, "order block sums")) != PANDA_OK) return cleanup(), st;
+        oa.keys = keys;
+        oa.hist = hist;
+        ce = cudaMemsetAsync(hist, 0, (size_t)nb * 4, stream);
+        if (ce != cudaSuccess) return cleanup(), cuda_fail(ce, "clear order histogram");
+        const unsigned gb = (unsigned)((m + 255) / 256);
+        k_order_keys<<<gb, 256, 0, stream>>>(oa);
+        if ((st = note_launch("k_order_keys")) != PANDA_OK) return cleanup(), st;
+        k_scan_blocks<<<nblk, 1024, 0, stream>>>(hist, nb, bsum);
+        if ((st = note_launch("k_scan_blocks")) != PANDA_OK) return cleanup(), st;
+        k_scan_sums<<<1, 1024, 0, stream>>>(bsum, nblk);
+        if ((st = note_launch("k_scan_sums")) != PANDA_OK) return cleanup(), st;
+        k_order_scatter<<<gb, 256, 0, stream>>>(keys, m, hist, bsum, perm);
+        if ((st = note_launch("k_order_scatter")) != PANDA_OK) return cleanup(), st;
+    }
+    timer.begin("query.traverse");
+    KnnArgs ka;
+    ka.nodes = t->nodes;
+    ka.pts = t->points;
+    ka.queries = queries;
+    ka.perm = perm;
+    ka.ids = ids;
+    ka.d2 = d2;
+    ka.err = err;
+    ka.m = m;
+    ka.num_nodes = t->num_nodes;
+    ka.npts = t->n;
+    ka.d = t->d;
+    ka.k = k;
+    st = launch_knn(ka, t->dp, k_class(k), stream);
+    if (st != PANDA_OK) return cleanup(), st;
+    timer.end();
+    if (host_err) {
+        ce = cudaMemcpyAsync(host_err, err, sizeof(unsigned), cudaMemcpyDeviceToHost, stream);
+        if (ce == cudaSuccess) ce = cudaStreamSynchronize(stream);
+        if (ce != cudaSuccess) return cleanup(), cuda_fail(ce, "query");
+    }
+    cleanup();
+    timer.finish();
+    return PANDA_OK;
+}
+
+}  // namespace panda

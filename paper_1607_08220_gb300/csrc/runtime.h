@@ -1,0 +1,88 @@
+// runtime.h -- host-side runtime of the library: tree object, error state,
+// launch accounting, phase timing, stream-ordered workspace.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "panda.h"
+
+struct panda_tree {
+    int64_t n = 0;
+    int32_t d = 0, dp = 0, bucket = 0;
+    int32_t nv = 0;           // float4 per packed point
+    int32_t ns = 0;           // float4 per node record
+    int32_t threshold = 0;    // subtree-stage threshold T
+    int device = 0;
+    float4* points = nullptr; // [n][nv], leaf order
+    float4* nodes = nullptr;  // [node_cap][ns]
+    int64_t node_cap = 0;
+    int64_t num_nodes = 0, num_leaves = 0;
+    int32_t depth = 0;
+    float root_lo[16] = {0}, root_hi[16] = {0};
+};
+
+namespace panda {
+
+// Thread-local last error text.
+void set_error(const char* fmt, ...);
+void clear_error();
+
+// Count one kernel launch (thread-local) and check the launch status.
+panda_status note_launch(const char* what);
+
+// Phase timing (CUDA events on the launching stream).
+struct PhaseTimer {
+    explicit PhaseTimer(cudaStream_t s);
+    ~PhaseTimer();
+    void begin(const char* name);   // ends the previous phase
+    void end();
+    void finish();                  // resolves events into the thread-local table
+  private:
+    cudaStream_t stream_;
+    bool on_;
+    int n_ = 0;
+    const char* names_[64];
+    cudaEvent_t ev_[65];
+    int64_t launches_at_[65];
+    bool open_ = false;
+};
+
+bool phase_timing_enabled();
+int64_t launches_so_far();
+
+// Convert a CUDA error into a status with a message.
+panda_status cuda_fail(cudaError_t e, const char* what);
+
+// Stream-ordered allocation from the device's default pool (cached across
+// calls: the pool keeps freed memory for reuse).
+panda_status ws_alloc(void** p, size_t bytes, cudaStream_t s, const char* what);
+void ws_free(void* p, cudaStream_t s);
+
+// Device pointer check: true if p is device memory (or managed) usable by kernels.
+bool is_device_ptr(const void* p);
+
+int num_sms();
+
+// Build and query entry points implemented in build.cu / query.cu.
+panda_status build_tree(const float* points, int64_t n, int32_t d, int32_t bucket,
+                        cudaStream_t stream, panda_tree** out);
+panda_status knn_query(const panda_tree* t, const float* queries, int64_t m, int32_t k,
+                       int32_t* ids, float* d2, const panda_query_params* params,
+                       cudaStream_t stream, unsigned* host_err);
+
+}  // namespace panda
+
+#define PANDA_CUDA(call, what)                                  \
+    do {                                                        \
+        cudaError_t _e = (call);                                \
+        if (_e != cudaSuccess) return panda::cuda_fail(_e, what); \
+    } while (0)
+
+#define PANDA_LAUNCHED(what)                                    \
+    do {                                                        \
+        panda_status _s = panda::note_launch(what);             \
+        if (_s != PANDA_OK) return _s;                          \
+    } while (0)

@@ -1,0 +1,302 @@
+"""Thin Python binding of the C ABI in include/panda.h (argument marshalling only).
+
+Every step of the build and the query runs in the CUDA library
+(``_lib/libpanda.so``); this module only passes pointers, sizes and streams.
+PyTorch provides device memory and streams.  There is no CPU fallback: if the
+library is missing or no GPU is present, calls raise :class:`PandaError`.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libpanda.so")
+
+ORDER = {"none": 0, "morton": 1, "leaf": 2}
+STATUS_NAMES = {0: "PANDA_OK", 1: "PANDA_ERR_INVALID_ARGUMENT", 2: "PANDA_ERR_NONFINITE_INPUT",
+                3: "PANDA_ERR_UNSUPPORTED", 4: "PANDA_ERR_OUT_OF_MEMORY", 5: "PANDA_ERR_CUDA",
+                6: "PANDA_ERR_TIMEOUT", 7: "PANDA_ERR_QUEUE_FULL", 8: "PANDA_ERR_DEPTH"}
+
+# Every symbol include/panda.h declares, with its ctypes signature.
+_P, _I32, _I64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+SIGNATURES = {
+    "panda_build": ([_P, _I64, _I32, _I32, ctypes.POINTER(_P)], ctypes.c_int),
+    "panda_build_async": ([_P, _I64, _I32, _I32, _P, ctypes.POINTER(_P)], ctypes.c_int),
+    "panda_build_host": ([_P, _I64, _I32, _I32, _P, ctypes.POINTER(_P)], ctypes.c_int),
+    "panda_knn": ([_P, _P, _I64, _I32, _P, _P], ctypes.c_int),
+    "panda_knn_async": ([_P, _P, _I64, _I32, _P, _P, _P, _P], ctypes.c_int),
+    "panda_knn_host": ([_P, _P, _I64, _I32, _P, _P, _P, _P], ctypes.c_int),
+    "panda_free": ([_P], None),
+    "panda_tree_get_info": ([_P, _P], ctypes.c_int),
+    "panda_tree_copy": ([_P, _P, _P], ctypes.c_int),
+    "panda_set_phase_timing": ([_I32], None),
+    "panda_phase_times": ([_P, _P, _P, _I32], _I32),
+    "panda_kernel_launches": ([], _I64),
+    "panda_status_string": ([ctypes.c_int], ctypes.c_char_p),
+    "panda_last_error": ([], ctypes.c_char_p),
+    "panda_version": ([], ctypes.c_char_p),
+}
+
+
+class PandaError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class QueryParams(ctypes.Structure):
+    _fields_ = [("order", ctypes.c_int32), ("lanes_per_query", ctypes.c_int32)]
+
+
+class TreeInfo(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("d", ctypes.c_int32), ("bucket", ctypes.c_int32),
+                ("num_nodes", ctypes.c_int64), ("num_leaves", ctypes.c_int64),
+                ("depth", ctypes.c_int32), ("node_floats", ctypes.c_int32),
+                ("point_floats", ctypes.c_int32), ("subtree_threshold", ctypes.c_int32),
+                ("device_bytes", ctypes.c_int64)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def load(path: str | None = None):
+    """Load libpanda.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise PandaError(5, f"CUDA library not built: {p} (run paper_1607_08220_gb300.build_ext)")
+        L = ctypes.CDLL(p)
+        for name, (args, res) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = L
+        return L
+
+
+def _check(st: int):
+    if st != 0:
+        msg = _lib.panda_last_error().decode(errors="replace")
+        raise PandaError(st, msg)
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_ptr(stream):
+    torch = _torch()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class Tree:
+    """A kd-tree resident in device memory (owns a C handle)."""
+
+    def __init__(self, handle: ctypes.c_void_p):
+        self._h = handle
+
+    @property
+    def handle(self):
+        return self._h
+
+    def info(self) -> dict:
+        inf = TreeInfo()
+        _check(_lib.panda_tree_get_info(self._h, ctypes.byref(inf)))
+        return {f: getattr(inf, f) for f, _ in TreeInfo._fields_}
+
+    def free(self):
+        if self._h:
+            _lib.panda_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    def raw(self):
+        """(nodes [num_nodes][node_floats] float32, points [n][point_floats] float32) on the host."""
+        inf = self.info()
+        nodes = np.empty((inf["num_nodes"], inf["node_floats"]), np.float32)
+        pts = np.empty((inf["n"], inf["point_floats"]), np.float32)
+        _check(_lib.panda_tree_copy(self._h, nodes.ctypes.data_as(ctypes.c_void_p),
+                                    pts.ctypes.data_as(ctypes.c_void_p)))
+        return nodes, pts
+
+    def export(self) -> dict:
+        """Canonical preorder form (the same layout the oracle exports)."""
+        inf = self.info()
+        d = inf["d"]
+        nodes, pts = self.raw()
+        return canonical_from_raw(nodes, pts, d)
+
+
+def padded_dim(d: int) -> int:
+    if d <= 2:
+        return 2
+    if d <= 4:
+        return d
+    if d <= 8:
+        return 8
+    if d <= 10:
+        return 10
+    return 16
+
+
+def canonical_from_raw(nodes: np.ndarray, pts: np.ndarray, d: int) -> dict:
+    """Walk the node table from the root in preorder; children of an inner node
+    are (a, a+1); a leaf covers packed points a .. a+b-1."""
+    dp = padded_dim(d)
+    hdr = nodes[:, :4].view(np.int32)
+    a_col, b_col, meta = hdr[:, 0], hdr[:, 1], hdr[:, 3].view(np.uint32)
+    split_col = nodes[:, 2]
+    order, depth, parent_slot = [], [], []
+    stack = [(0, 0)]
+    while stack:
+        i, dep = stack.pop()
+        order.append(i)
+        depth.append(dep)
+        if not meta[i] & 0x80000000:
+            c = int(a_col[i])
+            stack.append((c + 1, dep + 1))
+            stack.append((c, dep + 1))
+    order = np.asarray(order, np.int64)
+    pos = np.full(nodes.shape[0], -1, np.int64)
+    pos[order] = np.arange(order.size)
+    m = meta[order]
+    leaf = (m & 0x80000000) != 0
+    left = np.where(leaf, -1, pos[np.where(leaf, 0, a_col[order])])
+    right = np.where(leaf, -1, pos[np.where(leaf, 0, a_col[order] + 1)])
+    start = np.zeros(order.size, np.int64)
+    count = np.zeros(order.size, np.int64)
+    start[leaf] = a_col[order][leaf]
+    count[leaf] = b_col[order][leaf]
+    for j in range(order.size - 1, -1, -1):   # children follow their parent in preorder
+        if not leaf[j]:
+            start[j] = start[left[j]]
+            count[j] = count[left[j]] + count[right[j]]
+    ids = pts[:, dp].copy().view(np.int32)
+    return dict(leaf=leaf, index_split=((m & 0x40000000) != 0) & ~leaf,
+                dim=(m & 31).astype(np.int32), depth=np.asarray(depth, np.int32),
+                split=split_col[order].copy(), start=start, count=count, left=left, right=right,
+                lo=nodes[order, 4:4 + d].copy(), hi=nodes[order, 4 + dp:4 + dp + d].copy(),
+                perm=ids)
+
+
+def _as_device_points(x, what: str):
+    torch = _torch()
+    if not isinstance(x, torch.Tensor) or not x.is_cuda:
+        raise PandaError(1, f"{what} must be a CUDA tensor")
+    if x.dtype != torch.float32 or x.dim() != 2:
+        raise PandaError(1, f"{what} must be float32 [rows][d]")
+    return x.contiguous()
+
+
+def build(points, bucket: int = 32, stream=None, sync: bool = True) -> Tree:
+    """kd-tree over a CUDA float32 tensor [n][d] (Sec. III-A)."""
+    L = load()
+    pts = _as_device_points(points, "points")
+    h = ctypes.c_void_p()
+    _check(L.panda_build_async(ctypes.c_void_p(pts.data_ptr()), pts.shape[0], pts.shape[1], int(bucket),
+                               _stream_ptr(stream), ctypes.byref(h)))
+    t = Tree(h)
+    t._keep = pts if not sync else None
+    if sync:
+        (stream or _torch().cuda.current_stream()).synchronize()
+    return t
+
+
+def knn(tree: Tree, queries, k: int, order: str = "leaf", stream=None, out=None):
+    """Exact KNN (Algorithm 1, corrected) of every query row; enqueued on `stream`.
+
+    Returns (ids int32 [m][k], d2 float32 [m][k]) CUDA tensors."""
+    torch = _torch()
+    L = load()
+    q = _as_device_points(queries, "queries")
+    m = q.shape[0]
+    if out is None:
+        ids = torch.empty((m, k), dtype=torch.int32, device=q.device)
+        d2 = torch.empty((m, k), dtype=torch.float32, device=q.device)
+    else:
+        ids, d2 = out
+    prm = QueryParams(ORDER[order] if isinstance(order, str) else int(order), 1)
+    _check(L.panda_knn_async(tree.handle, ctypes.c_void_p(q.data_ptr()), m, int(k),
+                             ctypes.c_void_p(ids.data_ptr()), ctypes.c_void_p(d2.data_ptr()),
+                             ctypes.byref(prm), _stream_ptr(stream)))
+    return ids, d2
+
+
+def knn_sync(tree: Tree, queries, k: int):
+    """panda_knn: blocking query on the legacy stream; checks query finiteness."""
+    torch = _torch()
+    L = load()
+    q = _as_device_points(queries, "queries")
+    m = q.shape[0]
+    ids = torch.empty((m, k), dtype=torch.int32, device=q.device)
+    d2 = torch.empty((m, k), dtype=torch.float32, device=q.device)
+    torch.cuda.current_stream().synchronize()
+    _check(L.panda_knn(tree.handle, ctypes.c_void_p(q.data_ptr()), m, int(k),
+                       ctypes.c_void_p(ids.data_ptr()), ctypes.c_void_p(d2.data_ptr())))
+    return ids, d2
+
+
+def build_host(points: np.ndarray, bucket: int = 32, stream=None) -> Tree:
+    """panda_build_host: host points; the copy to the device is inside the call."""
+    L = load()
+    p = np.ascontiguousarray(points, dtype=np.float32)
+    h = ctypes.c_void_p()
+    _check(L.panda_build_host(p.ctypes.data_as(ctypes.c_void_p), p.shape[0], p.shape[1], int(bucket),
+                              _stream_ptr(stream), ctypes.byref(h)))
+    return Tree(h)
+
+
+def knn_host(tree: Tree, queries: np.ndarray, k: int, order: str = "leaf", stream=None,
+             out: tuple | None = None):
+    """panda_knn_host: host queries and outputs; copies in and out inside the call."""
+    L = load()
+    q = np.ascontiguousarray(queries, dtype=np.float32)
+    m = q.shape[0]
+    if out is None:
+        ids = np.empty((m, k), np.int32)
+        d2 = np.empty((m, k), np.float32)
+    else:
+        ids, d2 = out
+    prm = QueryParams(ORDER[order], 1)
+    _check(L.panda_knn_host(tree.handle, q.ctypes.data_as(ctypes.c_void_p), m, int(k),
+                            ids.ctypes.data_as(ctypes.c_void_p), d2.ctypes.data_as(ctypes.c_void_p),
+                            ctypes.byref(prm), _stream_ptr(stream)))
+    return ids, d2
+
+
+def set_phase_timing(on: bool):
+    load().panda_set_phase_timing(1 if on else 0)
+
+
+def phase_times() -> list[tuple[str, float, int]]:
+    L = load()
+    cap = 64
+    names = (ctypes.c_char_p * cap)()
+    ms = (ctypes.c_float * cap)()
+    ln = (ctypes.c_int32 * cap)()
+    n = L.panda_phase_times(names, ms, ln, cap)
+    return [(names[i].decode(), float(ms[i]), int(ln[i])) for i in range(min(n, cap))]
+
+
+def kernel_launches() -> int:
+    return int(load().panda_kernel_launches())
+
+
+def version() -> str:
+    return load().panda_version().decode()

@@ -1,0 +1,238 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Bars (stated by the result contract): neighbour ids bit-exact, FP32 squared
+distances identical to 0 ULP (compared as bit patterns), and the kd-tree
+identical node by node (split dimension, split value, ranges, boxes, leaf
+order).  Full-size workloads are checked on sampled queries against the
+oracle's exhaustive search plus tree invariants.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1607_08220_gb300 import workloads
+from tests import treecheck
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_1607_08220_gb300 import build_ext, panda
+    build_ext.build()
+    panda.load()
+    return panda
+
+
+def dev(x):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(x, dtype=np.float32)).cuda()
+
+
+def gpu_knn(P, tree, q, k, order="leaf"):
+    import torch
+    ids, d2 = P.knn(tree, dev(q), k, order=order)
+    torch.cuda.synchronize()
+    return ids.cpu().numpy(), d2.cpu().numpy()
+
+
+def assert_same_knn(ids, d2, eids, ed2):
+    assert ids.shape == eids.shape
+    bad = np.flatnonzero((ids != eids).any(axis=1))
+    assert bad.size == 0, f"{bad.size} rows differ, first {bad[:5]}: {ids[bad[0]]} vs {eids[bad[0]]}"
+    assert np.array_equal(d2.view(np.uint32), ed2.view(np.uint32)), "d2 not bit-identical"
+
+
+def full_parity(P, pts, q, k, B, orders=("leaf",), brute_rows=None):
+    t = P.build(dev(pts), B)
+    ot = oracle.build(pts, B)
+    g = t.export()
+    o = ot.export()
+    treecheck.assert_same_tree(g, o)
+    assert t.info()["depth"] == ot.depth
+    eids, ed2 = oracle.knn(ot, q, k)
+    for order in orders:
+        ids, d2 = gpu_knn(P, t, q, k, order)
+        assert_same_knn(ids, d2, eids, ed2)
+    if brute_rows is not None:
+        bi, bd = oracle.brute_knn(pts, q, k, rows=brute_rows)
+        assert_same_knn(eids[brute_rows], ed2[brute_rows], bi, bd)
+    return t, g
+
+
+# ------------------------------------------------------------------ small config
+
+
+def test_uniform_small_full_parity(P):
+    w = workloads.uniform_small()
+    t, g = full_parity(P, w.points, w.queries, w.k, w.bucket, orders=("leaf", "morton", "none"),
+                       brute_rows=np.arange(0, 10000, 7))
+    treecheck.check_invariants_fast(g, w.points, w.bucket)
+
+
+def _edge_cases():
+    rng = np.random.default_rng(11)
+    yield "n1", rng.random((1, 3), dtype=np.float32), rng.random((5, 3), dtype=np.float32), 4, 32
+    yield "single_bucket", rng.random((20, 3), dtype=np.float32), rng.random((40, 3), dtype=np.float32), 7, 32
+    yield "n_lt_k", rng.random((5, 2), dtype=np.float32), rng.random((33, 2), dtype=np.float32), 9, 4
+    yield "k_eq_n", rng.random((64, 3), dtype=np.float32), rng.random((70, 3), dtype=np.float32), 64, 8
+    lat = workloads.lattice_points(5000, 3, seed=5, side=6)
+    yield "lattice_ties", lat, workloads.lattice_points(333, 3, seed=6, side=6), 33, 16
+    yield "identical", np.full((2000, 3), 0.25, np.float32), rng.random((50, 3), dtype=np.float32), 5, 8
+    dup = np.repeat(rng.random((6, 3), dtype=np.float32), 700, axis=0)
+    yield "heavy_dups", dup, dup[::97], 17, 32
+    x = rng.random((3000, 4), dtype=np.float32)
+    x[:, 2] = 0.5
+    yield "constant_dim", x, rng.random((100, 4), dtype=np.float32), 12, 4
+    z = np.zeros((4096, 1), np.float32)
+    z[1::2] = 0.7
+    z[0::2] = 0.1
+    yield "sample_all_min", z, np.array([[0.3], [0.9], [0.1]], np.float32), 3, 256
+    for d in (1, 2, 5, 7, 8, 9, 12, 16):
+        yield f"gauss_d{d}", rng.standard_normal((6000, d)).astype(np.float32), \
+            rng.standard_normal((257, d)).astype(np.float32), 10, 32
+    for k in (1, 8, 9, 16, 17, 32, 33, 64):
+        yield f"k{k}", rng.random((9000, 3), dtype=np.float32), rng.random((100, 3), dtype=np.float32), k, 32
+    for B in (1, 2, 5, 64, 256):
+        yield f"B{B}", rng.random((5000, 3), dtype=np.float32), rng.random((99, 3), dtype=np.float32), 6, B
+    yield "neg_zero", np.array([[-0.0, 1.0], [0.0, 1.0], [0.0, -0.0], [-0.0, 0.0], [1.0, 1.0]] * 20,
+                               np.float32), np.array([[0.0, 0.0], [-0.0, 0.5]], np.float32), 7, 4
+
+
+@pytest.mark.parametrize("case", list(_edge_cases()), ids=lambda c: c[0])
+def test_edge_case_parity(P, case):
+    name, pts, q, k, B = case
+    full_parity(P, pts, q, k, B, orders=("leaf", "morton", "none"),
+                brute_rows=np.arange(q.shape[0]))
+
+
+def test_empty_query_batch(P):
+    import torch
+    pts = np.random.default_rng(0).random((100, 3), dtype=np.float32)
+    t = P.build(dev(pts), 8)
+    ids, d2 = P.knn(t, torch.empty((0, 3), dtype=torch.float32, device="cuda"), 5)
+    assert ids.shape == (0, 5)
+
+
+# ------------------------------------------------------------------ several levels and tiles
+
+
+def test_multilevel_cosmology_parity(P):
+    pts = workloads.cosmology_points(400_000, seed=9, halos=60)
+    q = workloads.cosmology_points(30_001, seed=10, halos=60)
+    t, g = full_parity(P, pts, q, 10, 32, orders=("leaf", "morton"), brute_rows=np.arange(0, 30001, 97))
+    treecheck.check_invariants_fast(g, pts, 32)
+    assert t.info()["depth"] <= treecheck.balance_bound(pts.shape[0], 32)
+
+
+def test_plasma_slab_parity(P):
+    pts = workloads.plasma_points(300_000, seed=4)
+    q = workloads.plasma_points(20_000, seed=7)
+    full_parity(P, pts, q, 8, 32, orders=("leaf",), brute_rows=np.arange(0, 20000, 101))
+
+
+def test_ten_dim_parity(P):
+    w = workloads.features_10d(n=150_000, m=5_000)
+    full_parity(P, w.points, w.queries, 16, 32, orders=("leaf", "morton"), brute_rows=np.arange(0, 5000, 23))
+
+
+# ------------------------------------------------------------------ full sizes (launch config of the benchmark)
+
+
+def test_cosmology_self_full_size(P):
+    """n = 2^24 self-KNN, k = 10, B = 32: tree identical to the oracle's; 2,000
+    sampled rows against exhaustive search; every point is its own rank-0
+    neighbour unless an exact duplicate with a smaller id exists."""
+    import torch
+    w = workloads.cosmology_self()
+    t = P.build(dev(w.points), w.bucket)
+    ids, d2 = P.knn(t, dev(w.points), w.k)
+    torch.cuda.synchronize()
+    ids, d2 = ids.cpu().numpy(), d2.cpu().numpy()
+    g = t.export()
+    treecheck.check_invariants_fast(g, w.points, w.bucket)
+    assert t.info()["depth"] <= treecheck.balance_bound(w.points.shape[0], w.bucket)
+    rows = np.random.default_rng(1).choice(w.points.shape[0], 2000, replace=False)
+    bi, bd = oracle.brute_knn(w.points, w.points, w.k, rows=rows)
+    assert_same_knn(ids[rows], d2[rows], bi, bd)
+    assert np.all(d2[:, 0] == 0.0)
+    u, first = np.unique(w.points, axis=0, return_index=True)
+    nodup = np.ones(w.points.shape[0], bool)
+    if u.shape[0] < w.points.shape[0]:
+        nodup[:] = False
+        nodup[first] = True
+    assert np.all(ids[nodup, 0] == np.flatnonzero(nodup))
+    ot = oracle.build(w.points, w.bucket)
+    treecheck.assert_same_tree(g, ot.export())
+
+
+def test_features_10d_full_size(P):
+    import torch
+    w = workloads.features_10d()
+    t = P.build(dev(w.points), 32)
+    ids, d2 = P.knn(t, dev(w.queries), w.k)
+    torch.cuda.synchronize()
+    ids, d2 = ids.cpu().numpy(), d2.cpu().numpy()
+    rows = np.random.default_rng(2).choice(w.queries.shape[0], 600, replace=False)
+    bi, bd = oracle.brute_knn(w.points, w.queries, w.k, rows=rows)
+    assert_same_knn(ids[rows], d2[rows], bi, bd)
+    treecheck.check_invariants_fast(t.export(), w.points, 32)
+
+
+# ------------------------------------------------------------------ API surface
+
+
+def test_host_variants_match(P):
+    w = workloads.uniform_small(n=50_000, m=3_000)
+    t = P.build_host(w.points, 32)
+    ids, d2 = P.knn_host(t, w.queries, 5)
+    t2 = P.build(dev(w.points), 32)
+    gi, gd = gpu_knn(P, t2, w.queries, 5)
+    assert_same_knn(ids, d2, gi, gd)
+    si, sd = P.knn_sync(t2, dev(w.queries), 5)
+    assert_same_knn(si.cpu().numpy(), sd.cpu().numpy(), gi, gd)
+
+
+def test_concurrent_streams_same_tree(P):
+    import torch
+    w = workloads.uniform_small(n=200_000, m=40_000)
+    t = P.build(dev(w.points), 32)
+    q = dev(w.queries)
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    torch.cuda.synchronize()
+    with torch.cuda.stream(s1):
+        a = P.knn(t, q, 9, stream=s1)
+    with torch.cuda.stream(s2):
+        b = P.knn(t, q, 9, stream=s2, order="morton")
+    torch.cuda.synchronize()
+    assert torch.equal(a[0], b[0]) and torch.equal(a[1].view(torch.int32), b[1].view(torch.int32))
+
+
+def test_errors_are_reported(P):
+    import torch
+    bad = np.random.default_rng(0).random((1000, 3), dtype=np.float32)
+    bad[17, 1] = np.nan
+    with pytest.raises(P.PandaError) as e:
+        P.build(dev(bad), 32)
+    assert e.value.status == 2
+    good = np.random.default_rng(1).random((1000, 3), dtype=np.float32)
+    t = P.build(dev(good), 32)
+    q = good[:50].copy()
+    q[3, 0] = np.inf
+    with pytest.raises(P.PandaError) as e:
+        P.knn_sync(t, dev(q), 4)
+    assert e.value.status == 2
+    with pytest.raises(P.PandaError) as e:
+        P.knn(t, dev(good[:10]), 65)
+    assert e.value.status == 3
+    import ctypes
+    L = P.load()
+    h = ctypes.c_void_p()
+    host = np.ascontiguousarray(good)
+    st = L.panda_build(host.ctypes.data_as(ctypes.c_void_p), 1000, 3, 32, ctypes.byref(h))
+    assert st == 1     # host pointer given to the device entry point
+    # the library stays usable after each error
+    ids, d2 = gpu_knn(P, t, good[:10], 3)
+    assert np.all(ids[:, 0] == np.arange(10))

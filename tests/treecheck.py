@@ -122,3 +122,68 @@ def _presplit_column(t: dict, pts: np.ndarray, node: int) -> np.ndarray:
     return pts[rows, int(t["dim"][node])]
 
 
+
+
+def check_invariants_fast(t: dict, points: np.ndarray, bucket: int):
+    """Vectorised form of check_invariants for large trees (one numpy pass per depth)."""
+    pts = np.asarray(points, np.float32)
+    n, d = pts.shape
+    perm = np.asarray(t["perm"], np.int64)
+    assert perm.shape == (n,) and perm.min() >= 0 and perm.max() < n
+    assert np.all(np.bincount(perm, minlength=n) == 1), "leaf order is not a permutation"
+    P = pts[perm]
+    leaf = np.asarray(t["leaf"], bool)
+    start, count = np.asarray(t["start"]), np.asarray(t["count"])
+    left, right = np.asarray(t["left"]), np.asarray(t["right"])
+    assert start[0] == 0 and count[0] == n
+    assert np.all(count[leaf] <= bucket) and np.all(count[leaf] >= 1)
+    inner = np.flatnonzero(~leaf)
+    assert np.all(count[inner] > bucket)
+    l, r = left[inner], right[inner]
+    assert np.all(start[l] == start[inner]) and np.all(start[r] == start[inner] + count[l])
+    assert np.all(count[l] + count[r] == count[inner]) and np.all(count[l] >= 1) and np.all(count[r] >= 1)
+    dep = np.asarray(t["depth"])
+    assert np.all(dep[l] == dep[inner] + 1) and np.all(dep[r] == dep[inner] + 1)
+    # leaf boxes tight, inner boxes = union of the children (hence tight)
+    lv = np.flatnonzero(leaf)
+    ls = start[lv]
+    assert np.all(np.diff(ls) > 0)
+    assert np.array_equal(t["lo"][lv], np.minimum.reduceat(P, ls, axis=0)), "leaf box lo not tight"
+    assert np.array_equal(t["hi"][lv], np.maximum.reduceat(P, ls, axis=0)), "leaf box hi not tight"
+    assert np.array_equal(t["lo"][inner], np.minimum(t["lo"][l], t["lo"][r]))
+    assert np.array_equal(t["hi"][inner], np.maximum(t["hi"][l], t["hi"][r]))
+    # stability inside leaves
+    steps = np.diff(perm)
+    boundary = np.zeros(n - 1, bool) if n > 1 else np.zeros(0, bool)
+    if n > 1:
+        boundary[ls[1:] - 1] = True
+        assert np.all((steps > 0) | boundary), "leaf not in stable order"
+    # sides of every split, one depth at a time
+    idx = np.flatnonzero(~leaf & ~np.asarray(t["index_split"], bool))
+    pos = np.arange(n)
+    for D in np.unique(dep[idx]):
+        nd = idx[dep[idx] == D]
+        nd = nd[np.argsort(start[nd])]
+        owner = np.searchsorted(start[nd], pos, side="right") - 1
+        ok = owner >= 0
+        o = nd[np.clip(owner, 0, None)]
+        ok &= pos < start[o] + count[o]
+        o, p = o[ok], pos[ok]
+        is_left = p < start[o] + count[left[o]]
+        x = P[p, t["dim"][o]]
+        s = np.asarray(t["split"], np.float32)[o]
+        assert np.all((x < s) == is_left), f"a point is on the wrong side of a depth-{D} split"
+    ix = np.flatnonzero(np.asarray(t["index_split"], bool) & ~leaf)
+    assert np.array_equal(t["lo"][ix], t["hi"][ix]), "index split over non-identical points"
+
+
+def assert_same_tree(a: dict, b: dict):
+    """Node-by-node structural equality of two canonical trees."""
+    assert len(a["leaf"]) == len(b["leaf"]), (len(a["leaf"]), len(b["leaf"]))
+    for key in ("leaf", "index_split", "start", "count", "left", "right", "depth"):
+        assert np.array_equal(np.asarray(a[key]), np.asarray(b[key])), key
+    inner = ~np.asarray(a["leaf"], bool)
+    assert np.array_equal(np.asarray(a["dim"])[inner], np.asarray(b["dim"])[inner]), "dim"
+    assert np.array_equal(np.asarray(a["split"])[inner], np.asarray(b["split"])[inner]), "split"
+    assert np.array_equal(a["lo"], b["lo"]) and np.array_equal(a["hi"], b["hi"]), "boxes"
+    assert np.array_equal(np.asarray(a["perm"]), np.asarray(b["perm"])), "leaf order"
