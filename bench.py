@@ -1,0 +1,421 @@
+#!/usr/bin/env python3
+"""Benchmark of the kd-tree build + exact KNN hot path on GB300.
+
+One step = build the kd-tree over the workload's points and answer every query
+(all §8(a) stages: transpose, level passes, subtree stage, packing, query
+ordering, traversal).  Default workload: cosmology-like self-KNN, n = 2^24
+points in 3-D, queries = the points, k = 10, B = 32.
+
+Prints ONE JSON line (rank 0).  `value` is whole-job queries/s (every query of
+every rank, each step including its tree build); `e2e` is the same measured
+through the host-buffer C-ABI calls (panda_build_host + panda_knn_host) with
+the host<->device copies inside the timed region.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "KNN queries/s + build pts/s on 1 GB300; served p50/p99 latency vs plain path"
+UNIT = "queries/s"
+CPU_SAMPLE = 1 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=["cosmology_self", "uniform_small", "features_10d"],
+                    default="cosmology_self")
+    ap.add_argument("--order", choices=["leaf", "morton", "none"], default="leaf")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--n", type=int, default=0, help="override n of cosmology_self (profiling runs)")
+    return ap.parse_args()
+
+
+def workload(name: str, n: int = 0):
+    from paper_1607_08220_gb300 import workloads
+    if name == "cosmology_self":
+        return workloads.cosmology_self(n=n) if n else workloads.cosmology_self()
+    if name == "uniform_small":
+        return workloads.uniform_small()
+    return workloads.features_10d()
+
+
+def workload_config(w, order):
+    n, d = w.points.shape
+    cfg = {"workload": f"{w.name}: n={n} d={d} m={w.queries.shape[0]} k={w.k} B={w.bucket}",
+           "n": n, "d": d, "m": int(w.queries.shape[0]), "k": w.k, "bucket": w.bucket,
+           "query_order": order, "parallelism": "replicas (one independent tree per GPU)",
+           "l2": f"inputs larger than L2 ({n * d * 4 / 1e6:.0f} MB points)" if n * d * 4 > 129e6
+           else "inputs fit in L2"}
+    return cfg
+
+
+# ----------------------------------------------------------------------------- clocks
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                    power.append(float(parts[3]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "samples": len(sm),
+                "power_w_max": max(power) if power else None, "reasons": sorted(reasons)}
+
+
+# ----------------------------------------------------------------------------- oracle (CPU)
+
+
+def cpu_oracle_step(pts, k, bucket, sample=CPU_SAMPLE):
+    """One bounded oracle step: build over the first `sample` points (a uniform
+    subsample: the workload rows are shuffled) and answer their self-queries."""
+    import oracle
+    sub = np.ascontiguousarray(pts[:sample])
+    t0 = time.perf_counter()
+    tree = oracle.build(sub, bucket)
+    t1 = time.perf_counter()
+    oracle.knn(tree, sub, k, threads=0)
+    t2 = time.perf_counter()
+    return sub.shape[0], t1 - t0, t2 - t1
+
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
+def cpu_baseline_obj(pts, k, bucket):
+    n, tb, tq = cpu_oracle_step(pts, k, bucket)
+    return {"value": n / (tb + tq), "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+            "cpu": cpu_model(),
+            "sample": f"oracle build (1 thread) + self-KNN (OpenMP, all cores) of the first {n} of "
+                      f"the {pts.shape[0]} workload points (same distribution), k={k}, B={bucket}",
+            "build_pts_per_s": n / tb, "query_per_s": n / tq, "build_s": tb, "query_s": tq}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.compile_oracle()
+    w = workload(args.workload, args.n)
+    pts = w.points
+    for _ in range(args.warmup):
+        cpu_oracle_step(pts, w.k, w.bucket)
+    t0 = time.perf_counter()
+    tb_sum = tq_sum = 0.0
+    n = 0
+    for _ in range(args.steps):
+        n, tb, tq = cpu_oracle_step(pts, w.k, w.bucket)
+        tb_sum += tb
+        tq_sum += tq
+    el = time.perf_counter() - t0
+    value = n * args.steps / el
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "config": workload_config(w, "n/a"),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+                             "cpu": cpu_model(),
+                             "sample": f"each step: oracle build + self-KNN of the first {n} workload points"},
+            "build_pts_per_s": n * args.steps / tb_sum, "query_per_s": n * args.steps / tq_sum,
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------- GPU arm
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            j = json.load(f)
+        return j, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def level_active_points(export: dict, threshold: int) -> list[int]:
+    """Points moved by the level passes at each depth: nodes with more than T points."""
+    cnt = np.asarray(export["count"])
+    dep = np.asarray(export["depth"])
+    big = cnt > threshold
+    out = []
+    for D in range(int(dep.max()) + 1 if cnt.size else 0):
+        s = int(cnt[big & (dep == D)].sum())
+        if s == 0:
+            break
+        out.append(s)
+    return out
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_1607_08220_gb300 as P
+    from paper_1607_08220_gb300 import build_ext
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    build_ext.build()
+    P.load()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    w = workload(args.workload, args.n)
+    n, d = w.points.shape
+    m = w.queries.shape[0]
+    k, B = w.k, w.bucket
+    self_q = w.queries is w.points
+    pts_dev = torch.from_numpy(w.points).cuda()
+    q_dev = pts_dev if self_q else torch.from_numpy(w.queries).cuda()
+    ids = torch.empty((m, k), dtype=torch.int32, device="cuda")
+    d2 = torch.empty((m, k), dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step():
+        t = P.build(pts_dev, B)
+        P.knn(t, q_dev, k, order=args.order, out=(ids, d2))
+        t.free()
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+
+    # ---- timed region (device time, CUDA events on the launching stream)
+    P.set_phase_timing(True)
+    phases: dict[str, list] = {}
+
+    def add_phases():
+        for name, ms, nl in P.phase_times():
+            e = phases.setdefault(name, [0.0, 0])
+            e[0] += ms
+            e[1] += nl
+
+    ev_b = [torch.cuda.Event(enable_timing=True) for _ in range(3 * args.steps)]
+    cvd = os.environ.get("CUDA_VISIBLE_DEVICES")
+    clocks = ClockSampler(cvd.split(",")[local].strip() if cvd else str(local))
+    clocks.start()
+    barrier()
+    torch.cuda.synchronize()
+    l0 = P.kernel_launches()
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    start.record(stream)
+    for s in range(args.steps):
+        ev_b[3 * s].record(stream)
+        t = P.build(pts_dev, B)
+        add_phases()
+        ev_b[3 * s + 1].record(stream)
+        P.knn(t, q_dev, k, order=args.order, out=(ids, d2))
+        add_phases()
+        ev_b[3 * s + 2].record(stream)
+        t.free()
+    end.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    launches = P.kernel_launches() - l0
+    clk = clocks.stop()
+    P.set_phase_timing(False)
+    el_ms = start.elapsed_time(end)
+    build_ms = sum(ev_b[3 * s].elapsed_time(ev_b[3 * s + 1]) for s in range(args.steps)) / args.steps
+    query_ms = sum(ev_b[3 * s + 1].elapsed_time(ev_b[3 * s + 2]) for s in range(args.steps)) / args.steps
+    el_max = el_ms
+    if world > 1:
+        tt = torch.tensor([el_ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        el_max = float(tt.item())
+    ms_per_step = el_max / args.steps
+    value = world * m * args.steps / (el_max / 1e3)
+
+    # ---- end to end through the host-buffer C-ABI calls
+    e2e = None
+    if not args.no_e2e:
+        pin_pts = torch.from_numpy(w.points).pin_memory()
+        pin_q = pin_pts if self_q else torch.from_numpy(w.queries).pin_memory()
+        pin_ids = torch.empty((m, k), dtype=torch.int32).pin_memory()
+        pin_d2 = torch.empty((m, k), dtype=torch.float32).pin_memory()
+        pn, qn, on = pin_pts.numpy(), pin_q.numpy(), (pin_ids.numpy(), pin_d2.numpy())
+
+        def step_e2e():
+            t = P.build_host(pn, B)
+            P.knn_host(t, qn, k, order=args.order, out=on)
+            t.free()
+
+        step_e2e()
+        barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            step_e2e()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        e_ms = e0.elapsed_time(e1)
+        if world > 1:
+            tt = torch.tensor([e_ms], device="cuda")
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            e_ms = float(tt.item())
+        e2e = {"value": world * m * args.steps / (e_ms / 1e3), "unit": UNIT,
+               "h2d_bytes_per_step": int(w.points.nbytes + w.queries.nbytes),
+               "d2h_bytes_per_step": int(m * k * 8), "ms_per_step": e_ms / args.steps}
+
+    # ---- roofline of the dominant kernel (outside the timed region: work counts)
+    peaks, peak_src = load_peaks()
+    per_step = {nm: (v[0] / args.steps, v[1] / args.steps) for nm, v in phases.items()}
+    kernel_phases = {"query.traverse": "k_knn", "level.partition": "k_partition", "subtree": "k_subtree",
+                     "level.hist": "k_hist", "transpose": "k_transpose"}
+    dom = max((p for p in per_step if p in kernel_phases), key=lambda p: per_step[p][0])
+    t = P.build(pts_dev, B)
+    info = t.info()
+    dom_ms, dom_launches = per_step[dom]
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    if dom == "query.traverse":
+        _, _, vis = P.knn_visits(t, q_dev, k, order=args.order)
+        torch.cuda.synchronize()
+        v = vis.to(torch.int64).sum(dim=0).cpu().numpy()
+        flops = 3.0 * d * float(v[0] + v[1])
+        sms = torch.cuda.get_device_properties(0).multi_processor_count
+        peak = sms * 128 * sm_max * 1e6 / 1e12
+        achieved = flops / (dom_ms / 1e3) / 1e12
+        roof = {"kernel": kernel_phases[dom], "bound": "alu", "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "algorithmic": f"3*d FP32 ops (sub, mul, add) per needed node box and per scanned bucket "
+                               f"point: nodes={int(v[0])} points={int(v[1])} per launch",
+                "peak_source": f"{sms} SMs x 128 FP32 lanes x {sm_max:.0f} MHz (derived)",
+                "ms_per_launch": dom_ms / max(dom_launches, 1)}
+    else:
+        exp = t.export()
+        act = level_active_points(exp, info["subtree_threshold"])
+        if dom == "level.partition":
+            byts = float(sum(act)) * 2 * (4 * d + 4)
+            desc = f"2*(4d+4) B per point per level pass; points per level {act}"
+        elif dom == "level.hist":
+            byts = float(sum(act)) * 4
+            desc = f"4 B per point per level pass; points per level {act}"
+        elif dom == "subtree":
+            byts = float(n) * (4 * d + 4 + info["point_floats"] * 4) + info["num_nodes"] * info["node_floats"] * 4
+            desc = "read (4d+4) B per point, write one packed record per point and per node"
+        else:
+            byts = float(n) * (8 * d + 4)
+            desc = "read 4d B, write 4d+4 B per point"
+        peak = float(peaks["hbm_gbs"])
+        achieved = byts / (dom_ms / 1e3) / 1e9
+        roof = {"kernel": kernel_phases[dom], "bound": "hbm", "achieved": achieved, "peak": peak,
+                "unit": "GB/s", "frac": achieved / peak, "traffic": None, "algorithmic": desc,
+                "peak_source": f"{peak_src} STREAM-style copy", "ms_per_launch": dom_ms / max(dom_launches, 1)}
+    roof["peak_note"] = f"of {peak_src}"
+    t.free()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline_obj(w.points, k, B)
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": workload_config(w, args.order), "clocks": clk, "e2e": e2e, "gpu_launches": launches,
+            "roofline": roof, "cpu_baseline": cpu,
+            "build_pts_per_s": world * n / (build_ms / 1e3), "query_per_s": world * m / (query_ms / 1e3),
+            "build_ms": build_ms, "query_ms": query_ms,
+            "phases_ms_per_step": {nm: round(v[0], 4) for nm, v in per_step.items()},
+            "tree": {"nodes": info["num_nodes"], "leaves": info["num_leaves"], "depth": info["depth"]}}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -71,8 +71,12 @@ typedef enum panda_order {
 } panda_order;
 
 typedef struct panda_query_params {
-    int32_t order;           /* panda_order; default PANDA_ORDER_LEAF */
-    int32_t lanes_per_query; /* 1 (default); reserved for split leaf scans */
+    int32_t order;          /* panda_order; default PANDA_ORDER_LEAF */
+    int32_t transpose_max;  /* scan shape: a leaf bucket needed by at most this many of
+                               a warp's 32 queries is scanned with lanes holding points
+                               (queries broadcast in turn), otherwise with lanes holding
+                               queries; 0 = default (12), 32 = always the former,
+                               -1 = always the latter.  Never changes results. */
 } panda_query_params;
 
 typedef struct panda_tree_info {
@@ -127,11 +131,13 @@ void panda_free(panda_tree* tree);
  * panda_tree_get_info fills *info.  panda_tree_copy copies the tree's node
  * records ([num_nodes][node_floats] floats) and packed points
  * ([n][point_floats] floats) to host buffers of those sizes (either may be
- * NULL).  Node record: int32 a, int32 b, float split, uint32 meta, then lo[d],
- * hi[d], zero padding; meta bit 31 = leaf, bit 30 = index split, bits 0..4 =
- * split dimension; an inner node's children are a and a+1; a leaf holds the
- * packed points a .. a+b-1.  Packed point: coordinates, then the point's id
- * as int32 bits in float slot d, zero padding. */
+ * NULL).  Let dp be d rounded up to the padded width (2, 3, 4, 8, 10 or 16);
+ * padded coordinates are 0.  Node record: int32 a, int32 b, float split,
+ * uint32 meta, then lo[dp], hi[dp], zero padding to a multiple of 4 floats;
+ * meta bit 31 = leaf, bit 30 = index split, bits 0..4 = split dimension; an
+ * inner node's children are nodes a and a+1; a leaf holds the packed points
+ * a .. a+b-1.  Packed point: dp coordinates, then the point's id as int32
+ * bits in float slot dp, zero padding to a multiple of 4 floats. */
 panda_status panda_tree_get_info(const panda_tree* tree, panda_tree_info* info);
 panda_status panda_tree_copy(const panda_tree* tree, float* host_nodes, float* host_points);
 
@@ -142,6 +148,13 @@ panda_status panda_tree_copy(const panda_tree* tree, float* host_nodes, float* h
  * that finished on this thread and returns how many there were. */
 void panda_set_phase_timing(int32_t enable);
 int32_t panda_phase_times(const char** names, float* ms, int32_t* launches, int32_t cap);
+/* Same as panda_knn_async, and also writes out_visits (device [m][2] int32):
+ * per query, the tree nodes whose bound did not exceed its k-th distance when
+ * popped, and the bucket points it scanned in those nodes -- the work
+ * Algorithm 1 needs for that query, used to state algorithmic FLOPs. */
+panda_status panda_knn_visits(const panda_tree* tree, const float* queries, int64_t m, int32_t k,
+                              int32_t* out_ids, float* out_d2, int32_t* out_visits,
+                              const panda_query_params* params, void* stream);
 /* Number of kernels this library launched on this thread so far. */
 int64_t panda_kernel_launches(void);
 

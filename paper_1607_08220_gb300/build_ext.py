@@ -2,9 +2,10 @@
 
 Every translation unit is compiled in parallel with nvcc for
 ``-gencode arch=compute_103a,code=sm_103a`` and linked into one shared library
-with an ``extern "C"`` ABI (include/panda.h).  ``--fmad=false`` keeps every
-floating-point multiply and add separately rounded, as the distance contract
-requires; no fast-math flags are used.
+with an ``extern "C"`` ABI (include/panda.h).  ``--fmad=false``, given to
+both the front end and ptxas, keeps every floating-point multiply and add
+separately rounded, as the distance contract requires (ptxas would otherwise
+fuse packed FP32x2 multiplies and adds); no fast-math flags are used.
 """
 from __future__ import annotations
 
@@ -22,10 +23,10 @@ INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(OUT_DIR, "libpanda.so")
 
-SOURCES = ["api.cu", "build.cu", "query.cu"]
+SOURCES = ["api.cu", "build.cu", "query.cu", "knn_lo.cu", "knn_hi.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--fmad=false", "-Xcompiler", "-fPIC",
-              "-Xcompiler", "-O2", "-I", INCLUDE, "-I", CSRC]
+NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--fmad=false", "-Xptxas", "--fmad=false",
+              "-Xcompiler", "-fPIC", "-Xcompiler", "-O2", "-I", INCLUDE, "-I", CSRC]
 
 
 def nvcc() -> str:

@@ -62,47 +62,42 @@ PhaseTimer::PhaseTimer(cudaStream_t s) : stream_(s), on_(g_timing) {}
 
 PhaseTimer::~PhaseTimer()
 {
-    if (!on_) return;
-    for (int i = 0; i < n_ + (open_ ? 1 : 0) && i < 65; i++)
-        if (ev_[i]) cudaEventDestroy(ev_[i]);
+    for (cudaEvent_t e : ev_) cudaEventDestroy(e);
+}
+
+void PhaseTimer::mark(const char* name)
+{
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+        cudaGetLastError();
+        on_ = false;
+        return;
+    }
+    cudaEventRecord(e, stream_);
+    ev_.push_back(e);
+    names_.push_back(name);
+    launches_at_.push_back(g_launches);
 }
 
 void PhaseTimer::begin(const char* name)
 {
-    if (!on_) return;
-    if (n_ >= 64) return;
-    if (!open_) {
-        cudaEventCreate(&ev_[0]);
-        cudaEventRecord(ev_[0], stream_);
-        launches_at_[0] = g_launches;
-        open_ = true;
-    } else {
-        cudaEventCreate(&ev_[n_ + 1]);
-        cudaEventRecord(ev_[n_ + 1], stream_);
-        launches_at_[n_ + 1] = g_launches;
-        n_++;
-    }
-    names_[n_] = name;
+    if (on_) mark(name);
 }
 
 void PhaseTimer::end()
 {
-    if (!on_ || !open_ || n_ >= 64) return;
-    cudaEventCreate(&ev_[n_ + 1]);
-    cudaEventRecord(ev_[n_ + 1], stream_);
-    launches_at_[n_ + 1] = g_launches;
-    n_++;
-    open_ = false;
+    if (on_ && !names_.empty() && names_.back() != nullptr) mark(nullptr);
 }
 
 void PhaseTimer::finish()
 {
     if (!on_) return;
-    if (open_) end();
+    end();
     g_phases.clear();
-    if (n_ == 0) return;
-    cudaEventSynchronize(ev_[n_]);
-    for (int i = 0; i < n_; i++) {
+    if (ev_.size() < 2) return;
+    cudaEventSynchronize(ev_.back());
+    for (size_t i = 0; i + 1 < ev_.size(); i++) {
+        if (!names_[i]) continue;
         float ms = 0.0f;
         cudaEventElapsedTime(&ms, ev_[i], ev_[i + 1]);
         int32_t l = (int32_t)(launches_at_[i + 1] - launches_at_[i]);
@@ -116,7 +111,7 @@ void PhaseTimer::finish()
             }
         if (!merged) g_phases.push_back({names_[i], ms, l});
     }
-    open_ = false;
+    cudaGetLastError();
 }
 
 int num_sms()
@@ -354,6 +349,24 @@ panda_status panda_knn_host(const panda_tree* tree, const float* queries, int64_
         return PANDA_ERR_NONFINITE_INPUT;
     }
     return st;
+}
+
+panda_status panda_knn_visits(const panda_tree* tree, const float* queries, int64_t m, int32_t k,
+                              int32_t* out_ids, float* out_d2, int32_t* out_visits,
+                              const panda_query_params* params, void* stream)
+{
+    clear_error();
+    if (!out_visits || (m > 0 && !is_device_ptr(out_visits))) {
+        set_error("panda_knn_visits: out_visits must be a device pointer");
+        return PANDA_ERR_INVALID_ARGUMENT;
+    }
+    try {
+        return knn_query(tree, queries, m, k, out_ids, out_d2, params, (cudaStream_t)stream, nullptr,
+                         out_visits);
+    } catch (...) {
+        set_error("panda_knn_visits: host exception");
+        return PANDA_ERR_OUT_OF_MEMORY;
+    }
 }
 
 void panda_free(panda_tree* tree)

@@ -1,0 +1,8 @@
+// knn_hi.cu -- traversal kernel instances for padded widths 8, 10 and 16.
+#include "knn_launch.cuh"
+
+namespace panda {
+template panda_status launch_knn_dp<8>(const KnnArgs&, int, cudaStream_t);
+template panda_status launch_knn_dp<10>(const KnnArgs&, int, cudaStream_t);
+template panda_status launch_knn_dp<16>(const KnnArgs&, int, cudaStream_t);
+}  // namespace panda

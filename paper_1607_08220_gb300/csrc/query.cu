@@ -145,26 +145,8 @@ __global__ void k_order_scatter(const unsigned* keys, long long m, int* cursor, 
     perm[p] = (int)i;
 }
 
-template <int DP, int KC>
-static panda_status launch_knn_t(const KnnArgs& a, cudaStream_t s)
-{
-    const long long warps = (a.m + 31) / 32;
-    const long long blocks = (warps + 3) / 4;
-    k_knn<DP, KC><<<(unsigned)blocks, 128, 0, s>>>(a);
-    PANDA_LAUNCHED("k_knn");
-    return PANDA_OK;
-}
-
 template <int DP>
-static panda_status launch_knn_dp(const KnnArgs& a, int kc, cudaStream_t s)
-{
-    switch (kc) {
-        case 8: return launch_knn_t<DP, 8>(a, s);
-        case 16: return launch_knn_t<DP, 16>(a, s);
-        case 32: return launch_knn_t<DP, 32>(a, s);
-        default: return launch_knn_t<DP, 64>(a, s);
-    }
-}
+panda_status launch_knn_dp(const KnnArgs& a, int kc, cudaStream_t s);
 
 static panda_status launch_knn(const KnnArgs& a, int dp, int kc, cudaStream_t s)
 {
@@ -178,17 +160,17 @@ static panda_status launch_knn(const KnnArgs& a, int dp, int kc, cudaStream_t s)
     }
 }
 
-static int k_class(int k)
+static int capacity_class(int k)
 {
-    if (k <= 8) return 8;
-    if (k <= 16) return 16;
-    if (k <= 32) return 32;
+    static const int cls[] = {4, 8, 12, 16, 24, 32, 48, 64};
+    for (int c : cls)
+        if (k <= c) return c;
     return 64;
 }
 
 panda_status knn_query(const panda_tree* t, const float* queries, int64_t m, int32_t k, int32_t* ids,
                        float* d2, const panda_query_params* params, cudaStream_t stream,
-                       unsigned* host_err)
+                       unsigned* host_err, int32_t* visits)
 {
     if (host_err) *host_err = 0;
     if (!t || m < 0 || k < 1 || (m > 0 && (!queries || !ids || !d2))) {
@@ -290,9 +272,11 @@ panda_status knn_query(const panda_tree* t, const float* queries, int64_t m, int
     ka.m = m;
     ka.num_nodes = t->num_nodes;
     ka.npts = t->n;
+    ka.visits = visits;
+    ka.transpose_max = (params && params->transpose_max != 0) ? params->transpose_max : 12;
     ka.d = t->d;
     ka.k = k;
-    st = launch_knn(ka, t->dp, k_class(k), stream);
+    st = launch_knn(ka, t->dp, capacity_class(k), stream);
     if (st != PANDA_OK) return cleanup(), st;
     timer.end();
     if (host_err) {

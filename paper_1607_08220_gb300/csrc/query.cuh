@@ -7,11 +7,20 @@
 // is skipped only when every lane's bound is strictly greater than its current
 // k-th distance (corrections C1, C3).  Inner nodes push the far child first
 // and the near child last (Algorithm 1 lines 20-24); the near side is the one
-// the majority of the lanes that need the node fall on.  A leaf bucket is
-// staged once into shared memory and scanned by all lanes (Sec. III-C: the
-// bucket scan is the SIMD-friendly part); each lane keeps its top-k list (the
-// heap H) sorted in registers as 64-bit keys (d2 bits << 32 | id), so the
-// radius r' is always the k-th key (correction C2).
+// the majority of the lanes that need the node fall on.
+//
+// A leaf bucket is staged once into shared memory, structure-of-arrays, and
+// scanned (Sec. III-C: the bucket scan is the SIMD-friendly part) in one of
+// two shapes, chosen per bucket by how many lanes need it:
+//   * many lanes: every lane computes its distance to all staged points
+//     (unrolled over the 32 staging slots, padded with far sentinels);
+//   * few lanes: the warp turns around -- lane j holds point j and the
+//     needing queries are broadcast one at a time -- so idle lanes do not
+//     pay for the scan.
+// Either shape only marks candidates whose distance does not exceed the
+// lane's current k-th distance; each lane then inserts its candidates with
+// the exact key (d2 bits << 32 | id) into its top-k list (the heap H), kept
+// sorted in registers, so the radius r' is always the k-th key (C2).
 #pragma once
 
 #include "common.cuh"
@@ -26,10 +35,12 @@ struct KnnArgs {
     int* ids;
     float* d2;
     unsigned* err;
+    int* visits;          // optional [m][2]: nodes and points each query needed
     long long m;
     long long num_nodes;
     long long npts;
     int d, k;
+    int transpose_max;    // use the transposed scan when at most this many lanes need a bucket
 };
 
 constexpr unsigned long long kKeyEmpty = (0x7f800000ull << 32) | 0xffffffffull;
@@ -45,34 +56,13 @@ __device__ __forceinline__ void topk_insert(unsigned long long (&s)[KC], unsigne
     s[0] = lt[0] ? c : s[0];
 }
 
-template <int DP>
-__device__ __forceinline__ float point_d2(const float (&q)[DP], const float4* p)
-{
-    float acc = 0.0f;
-#pragma unroll
-    for (int k = 0; k < DP; k++) {
-        const float4 v = p[k >> 2];
-        const float c = (k & 3) == 0 ? v.x : (k & 3) == 1 ? v.y : (k & 3) == 2 ? v.z : v.w;
-        const float t = __fsub_rn(q[k], c);
-        acc = __fadd_rn(acc, __fmul_rn(t, t));
-    }
-    return acc;
-}
-
-template <int DP>
-__device__ __forceinline__ int point_id(const float4* p)
-{
-    const float4 v = p[DP >> 2];
-    const float c = (DP & 3) == 0 ? v.x : (DP & 3) == 1 ? v.y : (DP & 3) == 2 ? v.z : v.w;
-    return __float_as_int(c);
-}
-
 template <int DP, int KC>
 __global__ void __launch_bounds__(128) k_knn(KnnArgs a)
 {
     constexpr int NV = (DP + 1 + 3) / 4;
     constexpr int NS = (4 + 2 * DP + 3) / 4;
-    __shared__ float4 stage[4][32 * NV];
+    __shared__ __align__(16) float stage_x[4][DP][32];
+    __shared__ int stage_id[4][32];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const long long g0 = ((long long)blockIdx.x * 4 + warp) * 32;
     if (g0 >= a.m) return;
@@ -92,13 +82,15 @@ __global__ void __launch_bounds__(128) k_knn(KnnArgs a)
 #pragma unroll
     for (int i = 0; i < KC; i++) s[i] = (valid && i >= KC - a.k) ? kKeyEmpty : 0ull;
 
+    float (*sx)[32] = stage_x[warp];
+    int* sid = stage_id[warp];
     int stack[kMaxDepth + 4];
     int sp = 0;
     stack[sp++] = 0;
-    float4* st = stage[warp];
     // A valid tree is visited in at most 2 * num_nodes pops; the cap only
     // guarantees termination (with an error flag) should a node table be corrupt.
     long long budget = 2LL * a.num_nodes + 8;
+    int vnodes = 0, vpts = 0;
     while (sp > 0) {
         if (--budget < 0 || (unsigned)stack[sp - 1] >= (unsigned)a.num_nodes) {
             if (lane == 0) atomicOr(a.err, kErrInternal);
@@ -115,16 +107,18 @@ __global__ void __launch_bounds__(128) k_knn(KnnArgs a)
             f[4 * r + 2] = v.z;
             f[4 * r + 3] = v.w;
         }
+        // bound: squared distance to the tight box, dims in order, unfused
         float bnd = 0.0f;
 #pragma unroll
         for (int k = 0; k < DP; k++) {
-            const float lo = f[4 + k], hi = f[4 + DP + k];
-            const float g = q[k] < lo ? __fsub_rn(lo, q[k]) : (q[k] > hi ? __fsub_rn(q[k], hi) : 0.0f);
+            const float g = fmaxf(fmaxf(__fsub_rn(f[4 + k], q[k]), __fsub_rn(q[k], f[4 + DP + k])), 0.0f);
             bnd = __fadd_rn(bnd, __fmul_rn(g, g));
         }
         const float kd = __uint_as_float((unsigned)(s[KC - 1] >> 32));
         const bool need = valid && !(bnd > kd);
-        if (!__any_sync(kFull, need)) continue;
+        const unsigned needm = __ballot_sync(kFull, need);
+        if (!needm) continue;
+        vnodes += need;
         const int h0 = __float_as_int(f[0]);
         const int h1 = __float_as_int(f[1]);
         const unsigned meta = __float_as_uint(f[3]);
@@ -139,25 +133,77 @@ __global__ void __launch_bounds__(128) k_knn(KnnArgs a)
                 if (lane < c) {
                     const float4* src = a.pts + (long long)(h0 + b0 + lane) * NV;
 #pragma unroll
-                    for (int v = 0; v < NV; v++) st[lane * NV + v] = __ldg(src + v);
+                    for (int v = 0; v < NV; v++) {
+                        const float4 p = __ldg(src + v);
+                        const float pv[4] = {p.x, p.y, p.z, p.w};
+#pragma unroll
+                        for (int e = 0; e < 4; e++) {
+                            const int k = 4 * v + e;
+                            if (k < DP) sx[k][lane] = pv[e];
+                            else if (k == DP) sid[lane] = __float_as_int(pv[e]);
+                        }
+                    }
+                } else {
+                    sx[0][lane] = INFINITY;   // sentinel: never within any radius
+#pragma unroll
+                    for (int k = 1; k < DP; k++) sx[k][lane] = 0.0f;
+                    sid[lane] = -1;
                 }
                 __syncwarp();
-                const unsigned long long kth = s[KC - 1];
-                unsigned mask = 0;
-                for (int j = 0; j < c; j++) {
-                    const float4* p = st + j * NV;
-                    const float dd = point_d2<DP>(q, p);
-                    const unsigned long long key =
-                        ((unsigned long long)__float_as_uint(dd) << 32) | (unsigned)point_id<DP>(p);
-                    if (key < kth) mask |= 1u << j;
+                if (need) vpts += c;
+                unsigned cand = 0;
+                if (__popc(needm) > a.transpose_max) {
+                    // every lane scans all 32 staged points (sentinels beyond c)
+#pragma unroll
+                    for (int j = 0; j < 32; j += 4) {
+                        float acc[4];
+#pragma unroll
+                        for (int k = 0; k < DP; k++) {
+                            const float4 x4 = *reinterpret_cast<const float4*>(&sx[k][j]);
+                            const float xv[4] = {x4.x, x4.y, x4.z, x4.w};
+#pragma unroll
+                            for (int e = 0; e < 4; e++) {
+                                const float t = __fsub_rn(q[k], xv[e]);
+                                acc[e] = k == 0 ? __fmul_rn(t, t) : __fadd_rn(acc[e], __fmul_rn(t, t));
+                            }
+                        }
+#pragma unroll
+                        for (int e = 0; e < 4; e++)
+                            if (acc[e] <= kd) cand |= 1u << (j + e);
+                    }
+                    if (!need) cand = 0;
+                } else {
+                    // lanes hold the points; needing queries are broadcast in turn
+                    float px[DP];
+#pragma unroll
+                    for (int k = 0; k < DP; k++) px[k] = sx[k][lane];
+                    unsigned rem = needm;
+                    while (rem) {
+                        const int L = __ffs(rem) - 1;
+                        rem &= rem - 1;
+                        const float kl = __shfl_sync(kFull, kd, L);
+                        float acc = 0.0f;
+#pragma unroll
+                        for (int k = 0; k < DP; k++) {
+                            const float t = __fsub_rn(__shfl_sync(kFull, q[k], L), px[k]);
+                            acc = k == 0 ? __fmul_rn(t, t) : __fadd_rn(acc, __fmul_rn(t, t));
+                        }
+                        const unsigned bits = __ballot_sync(kFull, acc <= kl);
+                        if (lane == L) cand = bits;
+                    }
                 }
-                while (mask) {
-                    const int j = __ffs(mask) - 1;
-                    mask &= mask - 1;
-                    const float4* p = st + j * NV;
-                    const float dd = point_d2<DP>(q, p);
+                // exact insertion of this lane's candidates
+                while (cand) {
+                    const int j = __ffs(cand) - 1;
+                    cand &= cand - 1;
+                    float acc = 0.0f;
+#pragma unroll
+                    for (int k = 0; k < DP; k++) {
+                        const float t = __fsub_rn(q[k], sx[k][j]);
+                        acc = k == 0 ? __fmul_rn(t, t) : __fadd_rn(acc, __fmul_rn(t, t));
+                    }
                     const unsigned long long key =
-                        ((unsigned long long)__float_as_uint(dd) << 32) | (unsigned)point_id<DP>(p);
+                        ((unsigned long long)__float_as_uint(acc) << 32) | (unsigned)sid[j];
                     if (key < s[KC - 1]) topk_insert<KC>(s, key);
                 }
             }
@@ -168,9 +214,8 @@ __global__ void __launch_bounds__(128) k_knn(KnnArgs a)
 #pragma unroll
             for (int k = 0; k < DP; k++)
                 if (k == dim) qd = q[k];
-            const unsigned bn = __ballot_sync(kFull, need);
             const unsigned br = __ballot_sync(kFull, need && qd >= sv);
-            const bool right_near = 2 * __popc(br) >= __popc(bn);
+            const bool right_near = 2 * __popc(br) >= __popc(needm);
             if (sp + 2 > kMaxDepth + 4) {
                 if (lane == 0) atomicOr(a.err, kErrInternal);
                 break;
@@ -178,6 +223,10 @@ __global__ void __launch_bounds__(128) k_knn(KnnArgs a)
             stack[sp++] = h0 + (right_near ? 0 : 1);   // far child first
             stack[sp++] = h0 + (right_near ? 1 : 0);   // near child last
         }
+    }
+    if (a.visits && valid) {
+        a.visits[2LL * qi] = vnodes;
+        a.visits[2LL * qi + 1] = vpts;
     }
     if (valid) {
         int* oi = a.ids + (long long)qi * a.k;

@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "panda.h"
 
@@ -33,21 +34,23 @@ void clear_error();
 // Count one kernel launch (thread-local) and check the launch status.
 panda_status note_launch(const char* what);
 
-// Phase timing (CUDA events on the launching stream).
+// Phase timing (CUDA events on the launching stream).  begin(name) starts a
+// phase (ending the previous one), end() closes the open phase; finish()
+// waits for the last event and adds every phase's time to the thread-local
+// table read by panda_phase_times (merged by name).
 struct PhaseTimer {
     explicit PhaseTimer(cudaStream_t s);
     ~PhaseTimer();
-    void begin(const char* name);   // ends the previous phase
+    void begin(const char* name);
     void end();
-    void finish();                  // resolves events into the thread-local table
+    void finish();
   private:
+    void mark(const char* name);
     cudaStream_t stream_;
     bool on_;
-    int n_ = 0;
-    const char* names_[64];
-    cudaEvent_t ev_[65];
-    int64_t launches_at_[65];
-    bool open_ = false;
+    std::vector<cudaEvent_t> ev_;
+    std::vector<const char*> names_;     // names_[i] = phase started by ev_[i] (nullptr: gap)
+    std::vector<int64_t> launches_at_;
 };
 
 bool phase_timing_enabled();
@@ -71,7 +74,7 @@ panda_status build_tree(const float* points, int64_t n, int32_t d, int32_t bucke
                         cudaStream_t stream, panda_tree** out);
 panda_status knn_query(const panda_tree* t, const float* queries, int64_t m, int32_t k,
                        int32_t* ids, float* d2, const panda_query_params* params,
-                       cudaStream_t stream, unsigned* host_err);
+                       cudaStream_t stream, unsigned* host_err, int32_t* visits = nullptr);
 
 }  // namespace panda
 

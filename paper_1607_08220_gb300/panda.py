@@ -30,6 +30,7 @@ SIGNATURES = {
     "panda_knn": ([_P, _P, _I64, _I32, _P, _P], ctypes.c_int),
     "panda_knn_async": ([_P, _P, _I64, _I32, _P, _P, _P, _P], ctypes.c_int),
     "panda_knn_host": ([_P, _P, _I64, _I32, _P, _P, _P, _P], ctypes.c_int),
+    "panda_knn_visits": ([_P, _P, _I64, _I32, _P, _P, _P, _P, _P], ctypes.c_int),
     "panda_free": ([_P], None),
     "panda_tree_get_info": ([_P, _P], ctypes.c_int),
     "panda_tree_copy": ([_P, _P, _P], ctypes.c_int),
@@ -49,7 +50,7 @@ class PandaError(RuntimeError):
 
 
 class QueryParams(ctypes.Structure):
-    _fields_ = [("order", ctypes.c_int32), ("lanes_per_query", ctypes.c_int32)]
+    _fields_ = [("order", ctypes.c_int32), ("transpose_max", ctypes.c_int32)]
 
 
 class TreeInfo(ctypes.Structure):
@@ -218,7 +219,7 @@ def build(points, bucket: int = 32, stream=None, sync: bool = True) -> Tree:
     return t
 
 
-def knn(tree: Tree, queries, k: int, order: str = "leaf", stream=None, out=None):
+def knn(tree: Tree, queries, k: int, order: str = "leaf", stream=None, out=None, transpose_max: int = 0):
     """Exact KNN (Algorithm 1, corrected) of every query row; enqueued on `stream`.
 
     Returns (ids int32 [m][k], d2 float32 [m][k]) CUDA tensors."""
@@ -231,11 +232,27 @@ def knn(tree: Tree, queries, k: int, order: str = "leaf", stream=None, out=None)
         d2 = torch.empty((m, k), dtype=torch.float32, device=q.device)
     else:
         ids, d2 = out
-    prm = QueryParams(ORDER[order] if isinstance(order, str) else int(order), 1)
+    prm = QueryParams(ORDER[order] if isinstance(order, str) else int(order), int(transpose_max))
     _check(L.panda_knn_async(tree.handle, ctypes.c_void_p(q.data_ptr()), m, int(k),
                              ctypes.c_void_p(ids.data_ptr()), ctypes.c_void_p(d2.data_ptr()),
                              ctypes.byref(prm), _stream_ptr(stream)))
     return ids, d2
+
+
+def knn_visits(tree: Tree, queries, k: int, order: str = "leaf", stream=None):
+    """KNN plus per-query work counts [m][2] (nodes needed, bucket points scanned)."""
+    torch = _torch()
+    L = load()
+    q = _as_device_points(queries, "queries")
+    m = q.shape[0]
+    ids = torch.empty((m, k), dtype=torch.int32, device=q.device)
+    d2 = torch.empty((m, k), dtype=torch.float32, device=q.device)
+    vis = torch.zeros((m, 2), dtype=torch.int32, device=q.device)
+    prm = QueryParams(ORDER[order], 0)
+    _check(L.panda_knn_visits(tree.handle, ctypes.c_void_p(q.data_ptr()), m, int(k),
+                              ctypes.c_void_p(ids.data_ptr()), ctypes.c_void_p(d2.data_ptr()),
+                              ctypes.c_void_p(vis.data_ptr()), ctypes.byref(prm), _stream_ptr(stream)))
+    return ids, d2, vis
 
 
 def knn_sync(tree: Tree, queries, k: int):
@@ -273,7 +290,7 @@ def knn_host(tree: Tree, queries: np.ndarray, k: int, order: str = "leaf", strea
         d2 = np.empty((m, k), np.float32)
     else:
         ids, d2 = out
-    prm = QueryParams(ORDER[order], 1)
+    prm = QueryParams(ORDER[order], 0)
     _check(L.panda_knn_host(tree.handle, q.ctypes.data_as(ctypes.c_void_p), m, int(k),
                             ids.ctypes.data_as(ctypes.c_void_p), d2.ctypes.data_as(ctypes.c_void_p),
                             ctypes.byref(prm), _stream_ptr(stream)))

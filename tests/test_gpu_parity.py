@@ -31,9 +31,9 @@ def dev(x):
     return torch.from_numpy(np.ascontiguousarray(x, dtype=np.float32)).cuda()
 
 
-def gpu_knn(P, tree, q, k, order="leaf"):
+def gpu_knn(P, tree, q, k, order="leaf", transpose_max=0):
     import torch
-    ids, d2 = P.knn(tree, dev(q), k, order=order)
+    ids, d2 = P.knn(tree, dev(q), k, order=order, transpose_max=transpose_max)
     torch.cuda.synchronize()
     return ids.cpu().numpy(), d2.cpu().numpy()
 
@@ -45,7 +45,7 @@ def assert_same_knn(ids, d2, eids, ed2):
     assert np.array_equal(d2.view(np.uint32), ed2.view(np.uint32)), "d2 not bit-identical"
 
 
-def full_parity(P, pts, q, k, B, orders=("leaf",), brute_rows=None):
+def full_parity(P, pts, q, k, B, orders=("leaf",), brute_rows=None, shapes=(0, -1, 32)):
     t = P.build(dev(pts), B)
     ot = oracle.build(pts, B)
     g = t.export()
@@ -55,6 +55,9 @@ def full_parity(P, pts, q, k, B, orders=("leaf",), brute_rows=None):
     eids, ed2 = oracle.knn(ot, q, k)
     for order in orders:
         ids, d2 = gpu_knn(P, t, q, k, order)
+        assert_same_knn(ids, d2, eids, ed2)
+    for shape in shapes:     # both leaf-scan shapes (lanes = queries, lanes = points)
+        ids, d2 = gpu_knn(P, t, q, k, orders[0], transpose_max=shape)
         assert_same_knn(ids, d2, eids, ed2)
     if brute_rows is not None:
         bi, bd = oracle.brute_knn(pts, q, k, rows=brute_rows)
@@ -106,6 +109,21 @@ def test_edge_case_parity(P, case):
     name, pts, q, k, B = case
     full_parity(P, pts, q, k, B, orders=("leaf", "morton", "none"),
                 brute_rows=np.arange(q.shape[0]))
+
+
+def test_phase_timing_many_levels(P):
+    """Phase timing across a build with many level passes (event bookkeeping)."""
+    pts = np.random.default_rng(4).random((3_000_000, 3), dtype=np.float32)
+    P.set_phase_timing(True)
+    try:
+        t = P.build(dev(pts), 8)
+        names = [p[0] for p in P.phase_times()]
+        assert "level.partition" in names and "subtree" in names
+        ids, d2 = gpu_knn(P, t, pts[:1000], 4)
+        assert "query.traverse" in [p[0] for p in P.phase_times()]
+    finally:
+        P.set_phase_timing(False)
+    assert np.all(ids[:, 0] == np.arange(1000))
 
 
 def test_empty_query_batch(P):
