@@ -354,7 +354,7 @@ def run_ours(args):
     dom_ms, dom_launches = per_step[dom]
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     if dom == "query.traverse":
-        _, _, vis = P.knn_visits(t, q_dev, k, order=args.order)
+        _, _, vis, kstats = P.knn_visits(t, q_dev, k, order=args.order)
         torch.cuda.synchronize()
         v = vis.to(torch.int64).sum(dim=0).cpu().numpy()
         flops = 3.0 * d * float(v[0] + v[1])
@@ -366,7 +366,7 @@ def run_ours(args):
                 "algorithmic": f"3*d FP32 ops (sub, mul, add) per needed node box and per scanned bucket "
                                f"point: nodes={int(v[0])} points={int(v[1])} per launch",
                 "peak_source": f"{sms} SMs x 128 FP32 lanes x {sm_max:.0f} MHz (derived)",
-                "ms_per_launch": dom_ms / max(dom_launches, 1)}
+                "ms_per_launch": dom_ms / max(dom_launches, 1), "events": kstats}
     else:
         exp = t.export()
         act = level_active_points(exp, info["subtree_threshold"])

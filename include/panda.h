@@ -90,6 +90,8 @@ typedef struct panda_tree_info {
     int32_t point_floats; /* floats per packed point (coordinates + id, padded to 4) */
     int32_t subtree_threshold; /* nodes of at most this many points were built in shared memory */
     int64_t device_bytes;      /* device memory held by the tree */
+    int64_t node_slots;        /* records in the node table: num_nodes plus unused
+                                  records no node refers to */
 } panda_tree_info;
 
 /* ---- construction: Sec. III-A (ii)-(iv) and Sec. III-A1 --------------------
@@ -129,7 +131,7 @@ void panda_free(panda_tree* tree);
 
 /* ---- inspection -------------------------------------------------------------
  * panda_tree_get_info fills *info.  panda_tree_copy copies the tree's node
- * records ([num_nodes][node_floats] floats) and packed points
+ * table ([node_slots][node_floats] floats) and packed points
  * ([n][point_floats] floats) to host buffers of those sizes (either may be
  * NULL).  Let dp be d rounded up to the padded width (2, 3, 4, 8, 10 or 16);
  * padded coordinates are 0.  Node record: int32 a, int32 b, float split,
@@ -148,13 +150,17 @@ panda_status panda_tree_copy(const panda_tree* tree, float* host_nodes, float* h
  * that finished on this thread and returns how many there were. */
 void panda_set_phase_timing(int32_t enable);
 int32_t panda_phase_times(const char** names, float* ms, int32_t* launches, int32_t cap);
-/* Same as panda_knn_async, and also writes out_visits (device [m][2] int32):
- * per query, the tree nodes whose bound did not exceed its k-th distance when
- * popped, and the bucket points it scanned in those nodes -- the work
- * Algorithm 1 needs for that query, used to state algorithmic FLOPs. */
+/* Same as panda_knn_async, and also writes (each optional, device memory):
+ * out_visits [m][2] int32: per query, the tree nodes whose bound did not
+ * exceed its k-th distance when popped, and the bucket points it scanned in
+ * those nodes -- the work Algorithm 1 needs for that query, used to state
+ * algorithmic FLOPs; out_stats [8] uint64, ADDED to (zero it first): warps,
+ * inner nodes, bucket chunks, chunks scanned with lanes = queries, query
+ * broadcasts of the lanes = points scan, insertion rounds, candidates,
+ * insertions (per-warp event counts of the traversal kernel). */
 panda_status panda_knn_visits(const panda_tree* tree, const float* queries, int64_t m, int32_t k,
                               int32_t* out_ids, float* out_d2, int32_t* out_visits,
-                              const panda_query_params* params, void* stream);
+                              uint64_t* out_stats, const panda_query_params* params, void* stream);
 /* Number of kernels this library launched on this thread so far. */
 int64_t panda_kernel_launches(void);
 

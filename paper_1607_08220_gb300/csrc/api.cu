@@ -353,16 +353,16 @@ panda_status panda_knn_host(const panda_tree* tree, const float* queries, int64_
 
 panda_status panda_knn_visits(const panda_tree* tree, const float* queries, int64_t m, int32_t k,
                               int32_t* out_ids, float* out_d2, int32_t* out_visits,
-                              const panda_query_params* params, void* stream)
+                              uint64_t* out_stats, const panda_query_params* params, void* stream)
 {
     clear_error();
-    if (!out_visits || (m > 0 && !is_device_ptr(out_visits))) {
-        set_error("panda_knn_visits: out_visits must be a device pointer");
+    if ((out_visits && m > 0 && !is_device_ptr(out_visits)) || (out_stats && !is_device_ptr(out_stats))) {
+        set_error("panda_knn_visits: out_visits and out_stats must be device pointers");
         return PANDA_ERR_INVALID_ARGUMENT;
     }
     try {
         return knn_query(tree, queries, m, k, out_ids, out_d2, params, (cudaStream_t)stream, nullptr,
-                         out_visits);
+                         out_visits, reinterpret_cast<unsigned long long*>(out_stats));
     } catch (...) {
         set_error("panda_knn_visits: host exception");
         return PANDA_ERR_OUT_OF_MEMORY;
@@ -393,6 +393,7 @@ panda_status panda_tree_get_info(const panda_tree* t, panda_tree_info* info)
     info->d = t->d;
     info->bucket = t->bucket;
     info->num_nodes = t->num_nodes;
+    info->node_slots = t->node_slots;
     info->num_leaves = t->num_leaves;
     info->depth = t->depth;
     info->node_floats = 4 * t->ns;
@@ -409,7 +410,7 @@ panda_status panda_tree_copy(const panda_tree* t, float* host_nodes, float* host
         return PANDA_ERR_INVALID_ARGUMENT;
     }
     if (host_nodes)
-        PANDA_CUDA(cudaMemcpy(host_nodes, t->nodes, (size_t)t->num_nodes * t->ns * 16, cudaMemcpyDeviceToHost),
+        PANDA_CUDA(cudaMemcpy(host_nodes, t->nodes, (size_t)t->node_slots * t->ns * 16, cudaMemcpyDeviceToHost),
                    "panda_tree_copy nodes");
     if (host_points)
         PANDA_CUDA(cudaMemcpy(host_points, t->points, (size_t)t->n * t->nv * 16, cudaMemcpyDeviceToHost),

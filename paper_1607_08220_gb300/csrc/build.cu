@@ -683,8 +683,8 @@ __global__ void k_partition(BuildArgs a, int L)
 // ------------------------------------------------------------------ A6 + A7
 
 struct WarpMem {
-    float* sx;            // [d][T] coordinates
-    int* sid;             // [T] ids
+    float* sx;            // [d][TS] coordinates (TS = T + 4: room for the 16-byte alignment offset)
+    int* sid;             // [TS] ids
     unsigned short* ix[2];  // [T] local indices, ping-pong
     int* rh;              // [256] radix histogram
     float* box;           // [2][kMaxDim] lo, hi
@@ -694,9 +694,20 @@ struct WarpMem {
 
 __host__ __device__ __forceinline__ size_t warp_bytes(int d, int T)
 {
-    size_t b = (size_t)4 * d * T + 4 * (size_t)T + 2 * 2 * (size_t)T + 256 * 4 + 3 * kMaxDim * 4;
+    const size_t TS = (size_t)T + 4;
+    size_t b = 4 * d * TS + 4 * TS + 2 * 2 * (size_t)T + 256 * 4 + 3 * kMaxDim * 4;
     b = (b + 15) & ~(size_t)15;
     return b + (kMaxDepth + 4) * sizeof(int4);
+}
+
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all()
+{
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
 }
 
 // Write node `node`'s record: header + box (lo, hi over dp slots, zero padded).
@@ -725,16 +736,21 @@ __device__ void write_node(const BuildArgs& a, int node, int4 hdr, const float* 
     }
 }
 
+// Node ids come in pairs (children a, a+1) from a per-warp pool refilled from
+// the global counter 64 ids at a time; ids left in a pool are holes in the
+// node table that nothing references.
+constexpr int kIdChunk = 64;
+
 __global__ void k_subtree(BuildArgs a, int wbytes)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int T = a.T, d = a.d;
+    const int T = a.T, d = a.d, TS = a.T + 4;
     unsigned char* base = smem + (size_t)warp * wbytes;
     WarpMem w;
     w.sx = reinterpret_cast<float*>(base);
-    w.sid = reinterpret_cast<int*>(w.sx + (size_t)d * T);
-    w.ix[0] = reinterpret_cast<unsigned short*>(w.sid + T);
+    w.sid = reinterpret_cast<int*>(w.sx + (size_t)d * TS);
+    w.ix[0] = reinterpret_cast<unsigned short*>(w.sid + TS);
     w.ix[1] = w.ix[0] + T;
     w.rh = reinterpret_cast<int*>(w.ix[1] + T);
     w.box = reinterpret_cast<float*>(w.rh + 256);
@@ -745,6 +761,8 @@ __global__ void k_subtree(BuildArgs a, int wbytes)
         w.stk = reinterpret_cast<int4*>(base + off);
     }
     const int nsmall = min(a.cnt[kCntSmall], a.small_cap);
+    int pool_next = 0, pool_end = 0;          // per-warp id pool (warp-uniform)
+    int my_nodes = 0, my_leaves = 0, my_depth = 0;
     for (;;) {
         int si = 0;
         if (lane == 0) si = atomicAdd(&a.cnt[kCntSmallNext], 1);
@@ -756,14 +774,25 @@ __global__ void k_subtree(BuildArgs a, int wbytes)
             if (lane == 0) atomicOr(a.err, kErrInternal);
             continue;
         }
-        const float* Xs = a.X[par];
-        for (int k = 0; k < d; k++)
-            for (int i = lane; i < count; i += 32)
-                w.sx[k * T + i] = Xs[(long long)k * a.n_pad + start + i];
-        for (int i = lane; i < count; i += 32) {
-            w.sid[i] = a.ID[par][start + i];
-            w.ix[0][i] = (unsigned short)i;
+        // stage the node: 16-byte asynchronous copies of the aligned superset of
+        // each column; element i of the node sits at offset off + i
+        const int off = start & 3;
+        const int g0 = start - off;
+        const int nch = (off + count + 3) >> 2;
+        {
+            const float* Xs = a.X[par];
+            for (int k = 0; k < d; k++) {
+                const float* src = Xs + (long long)k * a.n_pad + g0;
+                float* dst = w.sx + (size_t)k * TS;
+                for (int c = lane; c < nch; c += 32) cp_async16(dst + 4 * c, src + 4 * c);
+            }
+            const int* Is = a.ID[par] + g0;
+            for (int c = lane; c < nch; c += 32) cp_async16(w.sid + 4 * c, Is + 4 * c);
+            for (int i = lane; i < count; i += 32) w.ix[0][i] = (unsigned short)i;
+            cp_async_wait_all();
         }
+        const float* sxo = w.sx + off;
+        const int* sido = w.sid + off;
         int sp = 0;
         if (lane == 0) w.stk[0] = make_int4(0, count, sn.node, sn.depth_parity >> 1);
         sp = 1;
@@ -776,39 +805,37 @@ __global__ void k_subtree(BuildArgs a, int wbytes)
             const unsigned short* ixc = w.ix[rel & 1];
             unsigned short* ixn = w.ix[(rel + 1) & 1];
             const bool leaf = lc <= a.bucket || depth >= kMaxDepth;
-            {
-                // box (and, for inner nodes, the sample variance: every point is a sample)
-                for (int k = 0; k < d; k++) {
-                    const float* col = w.sx + k * T;
-                    float part = 0.0f, mn = INFINITY, mx = -INFINITY;
-                    for (int j = lane; j < lc; j += 32) {
-                        float x = col[ixc[ls + j]];
-                        part = __fadd_rn(part, x);
-                        mn = fminf(mn, x);
-                        mx = fmaxf(mx, x);
-                    }
-                    mn = warp_min(mn);
-                    mx = warp_max(mx);
-                    float vk = 0.0f;
-                    if (!leaf) {
-                        float mean = __fdiv_rn(fixed_order_warp_total(part), (float)lc);
-                        float p2 = 0.0f;
-                        for (int j = lane; j < lc; j += 32) {
-                            float c = __fsub_rn(col[ixc[ls + j]], mean);
-                            p2 = __fadd_rn(p2, __fmul_rn(c, c));
-                        }
-                        vk = __fdiv_rn(fixed_order_warp_total(p2), (float)lc);
-                    }
-                    if (lane == 0) {
-                        w.box[k] = mn;
-                        w.box[kMaxDim + k] = mx;
-                        w.var[k] = vk;
-                    }
+            // box (and, for inner nodes, the sample variance: every point is a sample)
+            for (int k = 0; k < d; k++) {
+                const float* col = sxo + (size_t)k * TS;
+                float part = 0.0f, mn = INFINITY, mx = -INFINITY;
+                for (int j = lane; j < lc; j += 32) {
+                    float x = col[ixc[ls + j]];
+                    part = __fadd_rn(part, x);
+                    mn = fminf(mn, x);
+                    mx = fmaxf(mx, x);
                 }
-                __syncwarp();
+                mn = warp_min(mn);
+                mx = warp_max(mx);
+                float vk = 0.0f;
+                if (!leaf) {
+                    float mean = __fdiv_rn(fixed_order_warp_total(part), (float)lc);
+                    float p2 = 0.0f;
+                    for (int j = lane; j < lc; j += 32) {
+                        float c = __fsub_rn(col[ixc[ls + j]], mean);
+                        p2 = __fadd_rn(p2, __fmul_rn(c, c));
+                    }
+                    vk = __fdiv_rn(fixed_order_warp_total(p2), (float)lc);
+                }
+                if (lane == 0) {
+                    w.box[k] = mn;
+                    w.box[kMaxDim + k] = mx;
+                    w.var[k] = vk;
+                }
             }
+            __syncwarp();
             if (leaf) {
-                if (lc > a.bucket) atomicOr(a.err, kErrDepth);
+                if (lc > a.bucket && lane == 0) atomicOr(a.err, kErrDepth);
                 const int pstart = start + ls;
                 write_node(a, node, make_int4(pstart, lc, 0, (int)kMetaLeaf), w.box);
                 for (int i = lane; i < lc; i += 32) {
@@ -820,17 +847,16 @@ __global__ void k_subtree(BuildArgs a, int wbytes)
                         for (int q = 0; q < 4; q++) {
                             int slot = 4 * v4 + q;
                             float val = 0.0f;
-                            if (slot < d) val = w.sx[slot * T + p];
-                            else if (slot == a.dp) val = __int_as_float(w.sid[p]);
+                            if (slot < d) val = sxo[(size_t)slot * TS + p];
+                            else if (slot == a.dp) val = __int_as_float(sido[p]);
                             f[q] = val;
                         }
                         o[v4] = make_float4(f[0], f[1], f[2], f[3]);
                     }
                 }
-                if (lane == 0) {
-                    atomicAdd(&a.cnt[kCntLeaves], 1);
-                    atomicMax(&a.cnt[kCntDepth], depth);
-                }
+                my_nodes++;
+                my_leaves++;
+                my_depth = max(my_depth, depth);
                 __syncwarp();
                 continue;
             }
@@ -838,16 +864,27 @@ __global__ void k_subtree(BuildArgs a, int wbytes)
             int dim = argmax_dims(w.var, d, 0u);
             int mode = -1, cleft = 0;
             float s = 0.0f;
-            if (w.var[dim] > 0.0f) {
-                const float* col = w.sx + dim * T;
+            if (w.var[dim] > 0.0f && w.box[kMaxDim + dim] > w.box[dim]) {
+                const float* col = sxo + (size_t)dim * TS;
+                // radix select of rank floor(lc/2) on order-preserving keys; the
+                // bits above the highest bit where the node's min and max keys
+                // differ are common to every key and are skipped
+                // (keys of x + 0: -0 and +0 compare equal as floats and get one key)
+                const uint32_t kmin = float_key(__fadd_rn(w.box[dim], 0.0f));
+                const uint32_t kmax = float_key(__fadd_rn(w.box[kMaxDim + dim], 0.0f));
+                const int top = 32 - __clz(kmin ^ kmax);
                 int rank = lc >> 1;
-                uint32_t prefix = 0, mask = 0;
-                for (int shift = 24; shift >= 0; shift -= 8) {
+                uint32_t mask = (top >= 32) ? 0u : ~((1u << top) - 1u);
+                uint32_t prefix = kmin & mask;
+                for (int hi = top; hi > 0; hi -= 8) {
+                    const int shift = hi >= 8 ? hi - 8 : 0;
+                    const int width = hi - shift;
+                    const uint32_t dmask = (1u << width) - 1u;
                     for (int b = lane; b < 256; b += 32) w.rh[b] = 0;
                     __syncwarp();
                     for (int j = lane; j < lc; j += 32) {
-                        uint32_t key = float_key(col[ixc[ls + j]]);
-                        if ((key & mask) == prefix) atomicAdd(&w.rh[(key >> shift) & 255], 1);
+                        uint32_t key = float_key(__fadd_rn(col[ixc[ls + j]], 0.0f));
+                        if ((key & mask) == prefix) atomicAdd(&w.rh[(key >> shift) & dmask], 1);
                     }
                     __syncwarp();
                     int loc = 0;
@@ -873,7 +910,7 @@ __global__ void k_subtree(BuildArgs a, int wbytes)
                     int digit = __shfl_sync(kFull, found, src);
                     below = __shfl_sync(kFull, below, src);
                     prefix |= (uint32_t)digit << shift;
-                    mask |= 0xffu << shift;
+                    mask |= dmask << shift;
                     rank -= below;
                     __syncwarp();
                 }
@@ -914,7 +951,7 @@ __global__ void k_subtree(BuildArgs a, int wbytes)
                     used |= 1u << k;
                     const float mn = w.box[k], mx = w.box[kMaxDim + k];
                     if (mx > mn) {
-                        const float* col = w.sx + k * T;
+                        const float* col = sxo + (size_t)k * TS;
                         float nxt = INFINITY;
                         for (int j = lane; j < lc; j += 32) {
                             float x = col[ixc[ls + j]];
@@ -938,7 +975,7 @@ __global__ void k_subtree(BuildArgs a, int wbytes)
             }
             // ---- stable partition by warp ballots
             {
-                const float* col = w.sx + dim * T;
+                const float* col = sxo + (size_t)dim * TS;
                 const int half = (lc + 1) >> 1;
                 int lcnt = 0, rcnt = 0;
                 for (int b0 = 0; b0 < lc; b0 += 32) {
@@ -956,12 +993,18 @@ __global__ void k_subtree(BuildArgs a, int wbytes)
                 }
                 if (lane == 0 && lcnt != cleft) atomicOr(a.err, kErrInternal);
             }
-            int c0 = 0;
-            if (lane == 0) c0 = atomicAdd(&a.cnt[kCntNodes], 2);
-            c0 = __shfl_sync(kFull, c0, 0);
-            if (c0 + 2 > a.node_cap && lane == 0) atomicOr(a.err, kErrNodeOverflow);
+            if (pool_next + 2 > pool_end) {
+                int c0 = 0;
+                if (lane == 0) c0 = atomicAdd(&a.cnt[kCntNodes], kIdChunk);
+                pool_next = __shfl_sync(kFull, c0, 0);
+                pool_end = pool_next + kIdChunk;
+                if (pool_end > a.node_cap && lane == 0) atomicOr(a.err, kErrNodeOverflow);
+            }
+            const int c0 = pool_next;
+            pool_next += 2;
             unsigned meta = (unsigned)dim | (mode == kModeIndex ? kMetaIndex : 0u);
             write_node(a, node, make_int4(c0, 0, __float_as_int(s), (int)meta), w.box);
+            my_nodes++;
             __syncwarp();
             if (lane == 0) {
                 const int ew = (depth + 1) | ((rel + 1) << 16);
@@ -971,6 +1014,11 @@ __global__ void k_subtree(BuildArgs a, int wbytes)
             sp += 2;
             __syncwarp();
         }
+    }
+    if (lane == 0 && my_nodes) {
+        atomicAdd(&a.cnt[kCntRealNodes], my_nodes);
+        atomicAdd(&a.cnt[kCntLeaves], my_leaves);
+        atomicMax(&a.cnt[kCntDepth], my_depth);
     }
 }
 
@@ -1160,6 +1208,7 @@ panda_status build_once(const float* points, int n, int d, int bucket, cudaStrea
     *err_out = herr;
     if (herr) return PANDA_OK;   // caller decides (retry or error)
     const int nlevels = hc[kCntLevels];
+    const long long level_ids = hc[kCntNodes], n_small = hc[kCntSmall];
 
     timer.begin("subtree");
     {
@@ -1180,7 +1229,10 @@ panda_status build_once(const float* points, int n, int d, int bucket, cudaStrea
     timer.finish();
     *need_nodes = hc[kCntNodes];
     *err_out = herr;
-    t->num_nodes = hc[kCntNodes];
+    // ids below level_ids belong to the level stage (subtree roots included,
+    // which the subtree stage counts again); the rest of the table may hold holes
+    t->node_slots = hc[kCntNodes];
+    t->num_nodes = level_ids + hc[kCntRealNodes] - n_small;
     t->num_leaves = hc[kCntLeaves];
     t->depth = hc[kCntDepth];
     return PANDA_OK;
@@ -1223,8 +1275,11 @@ panda_status build_tree(const float* points, int64_t n64, int32_t d, int32_t buc
     pl.small_cap = 4 * pl.act_cap + 16;
     pl.lvl_stride = pl.act_cap;
     pl.max_levels = kMaxDepth + 1;
-    pl.node_cap = 4LL * n / bucket + 8LL * pl.act_cap + 1024;
-    pl.node_cap = std::min<long long>(pl.node_cap, 2LL * n + 8);
+    // holes: each subtree warp may leave up to kIdChunk unused ids
+    const long long hole_slack = (long long)num_sms() * 8 * kIdChunk;
+    const long long node_max = 2LL * n + 8 + hole_slack;
+    pl.node_cap = 4LL * n / bucket + 8LL * pl.act_cap + 1024 + hole_slack;
+    pl.node_cap = std::min<long long>(pl.node_cap, node_max);
     for (int attempt = 0; attempt < 3; attempt++) {
         t->node_cap = pl.node_cap;
         void* pn = nullptr;
@@ -1255,7 +1310,7 @@ panda_status build_tree(const float* points, int64_t n64, int32_t d, int32_t buc
                 st = PANDA_ERR_CUDA;
             } else {
                 if (err & kErrSmallOverflow) pl.small_cap = std::max(pl.small_cap * 2, need_small + 16);
-                if (err & kErrNodeOverflow) pl.node_cap = std::min<long long>(2LL * n + 8, std::max(pl.node_cap * 2, need_nodes + 16));
+                if (err & kErrNodeOverflow) pl.node_cap = std::min<long long>(node_max, std::max(pl.node_cap * 2, need_nodes + 16));
                 retry = true;
             }
         }

@@ -75,6 +75,7 @@ enum : int {
     kCntLeaves = 7,
     kCntDepth = 8,
     kCntLevels = 9,    // number of level-stage levels that had active nodes
+    kCntRealNodes = 10, // nodes written by the subtree stage (the rest of its id range are holes)
     kCntSlots = 16,
 };
 

@@ -2,7 +2,7 @@
 #include "knn_launch.cuh"
 
 namespace panda {
-template panda_status launch_knn_dp<8>(const KnnArgs&, int, cudaStream_t);
-template panda_status launch_knn_dp<10>(const KnnArgs&, int, cudaStream_t);
-template panda_status launch_knn_dp<16>(const KnnArgs&, int, cudaStream_t);
+template panda_status launch_knn_dp<8>(const KnnArgs&, cudaStream_t);
+template panda_status launch_knn_dp<10>(const KnnArgs&, cudaStream_t);
+template panda_status launch_knn_dp<16>(const KnnArgs&, cudaStream_t);
 }  // namespace panda

@@ -146,31 +146,23 @@ __global__ void k_order_scatter(const unsigned* keys, long long m, int* cursor, 
 }
 
 template <int DP>
-panda_status launch_knn_dp(const KnnArgs& a, int kc, cudaStream_t s);
+panda_status launch_knn_dp(const KnnArgs& a, cudaStream_t s);
 
-static panda_status launch_knn(const KnnArgs& a, int dp, int kc, cudaStream_t s)
+static panda_status launch_knn(const KnnArgs& a, int dp, cudaStream_t s)
 {
     switch (dp) {
-        case 2: return launch_knn_dp<2>(a, kc, s);
-        case 3: return launch_knn_dp<3>(a, kc, s);
-        case 4: return launch_knn_dp<4>(a, kc, s);
-        case 8: return launch_knn_dp<8>(a, kc, s);
-        case 10: return launch_knn_dp<10>(a, kc, s);
-        default: return launch_knn_dp<16>(a, kc, s);
+        case 2: return launch_knn_dp<2>(a, s);
+        case 3: return launch_knn_dp<3>(a, s);
+        case 4: return launch_knn_dp<4>(a, s);
+        case 8: return launch_knn_dp<8>(a, s);
+        case 10: return launch_knn_dp<10>(a, s);
+        default: return launch_knn_dp<16>(a, s);
     }
-}
-
-static int capacity_class(int k)
-{
-    static const int cls[] = {4, 8, 12, 16, 24, 32, 48, 64};
-    for (int c : cls)
-        if (k <= c) return c;
-    return 64;
 }
 
 panda_status knn_query(const panda_tree* t, const float* queries, int64_t m, int32_t k, int32_t* ids,
                        float* d2, const panda_query_params* params, cudaStream_t stream,
-                       unsigned* host_err, int32_t* visits)
+                       unsigned* host_err, int32_t* visits, unsigned long long* stats)
 {
     if (host_err) *host_err = 0;
     if (!t || m < 0 || k < 1 || (m > 0 && (!queries || !ids || !d2))) {
@@ -216,7 +208,7 @@ panda_status knn_query(const panda_tree* t, const float* queries, int64_t m, int
         OrderArgs oa;
         memset(&oa, 0, sizeof(oa));
         oa.nodes = t->nodes;
-        oa.num_nodes = t->num_nodes;
+        oa.num_nodes = t->node_slots;
         oa.queries = queries;
         oa.m = m;
         oa.d = t->d;
@@ -270,13 +262,14 @@ panda_status knn_query(const panda_tree* t, const float* queries, int64_t m, int
     ka.d2 = d2;
     ka.err = err;
     ka.m = m;
-    ka.num_nodes = t->num_nodes;
+    ka.num_nodes = t->node_slots;
     ka.npts = t->n;
     ka.visits = visits;
+    ka.stats = stats;
     ka.transpose_max = (params && params->transpose_max != 0) ? params->transpose_max : 12;
     ka.d = t->d;
     ka.k = k;
-    st = launch_knn(ka, t->dp, capacity_class(k), stream);
+    st = launch_knn(ka, t->dp, stream);
     if (st != PANDA_OK) return cleanup(), st;
     timer.end();
     if (host_err) {

@@ -18,9 +18,11 @@
 //     needing queries are broadcast one at a time -- so idle lanes do not
 //     pay for the scan.
 // Either shape only marks candidates whose distance does not exceed the
-// lane's current k-th distance; each lane then inserts its candidates with
-// the exact key (d2 bits << 32 | id) into its top-k list (the heap H), kept
-// sorted in registers, so the radius r' is always the k-th key (C2).
+// lane's current k-th distance.  Each lane then inserts its candidates with
+// the exact key (d2 bits << 32 | id) into its heap H of the k best keys: a
+// max-heap in shared memory (interleaved by lane, so the lanes of a warp hit
+// distinct banks), whose root is the radius r' (correction C2).  At the end
+// the heap is emptied in order into the output row.
 #pragma once
 
 #include "common.cuh"
@@ -36,6 +38,7 @@ struct KnnArgs {
     float* d2;
     unsigned* err;
     int* visits;          // optional [m][2]: nodes and points each query needed
+    unsigned long long* stats;  // optional [8] event counters (diagnostics)
     long long m;
     long long num_nodes;
     long long npts;
@@ -44,27 +47,37 @@ struct KnnArgs {
 };
 
 constexpr unsigned long long kKeyEmpty = (0x7f800000ull << 32) | 0xffffffffull;
+constexpr int kKnnThreads = 128;
 
-template <int KC>
-__device__ __forceinline__ void topk_insert(unsigned long long (&s)[KC], unsigned long long c)
+// Replace the root of the lane's max-heap h[0..k) (stride kKnnThreads) by c
+// and sift it down.  Keys are unique, so c never equals a child.
+__device__ __forceinline__ void heap_replace_root(unsigned long long* h, int k, unsigned long long c)
 {
-    bool lt[KC];
-#pragma unroll
-    for (int i = 0; i < KC; i++) lt[i] = c < s[i];
-#pragma unroll
-    for (int i = KC - 1; i >= 1; i--) s[i] = lt[i - 1] ? s[i - 1] : (lt[i] ? c : s[i]);
-    s[0] = lt[0] ? c : s[0];
+    int i = 0;
+    for (;;) {
+        const int l = 2 * i + 1;
+        if (l >= k) break;
+        const unsigned long long cl = h[l * kKnnThreads];
+        const unsigned long long cr = (l + 1 < k) ? h[(l + 1) * kKnnThreads] : 0ull;
+        const bool right = cr > cl;
+        const unsigned long long cm = right ? cr : cl;
+        if (cm < c) break;
+        h[i * kKnnThreads] = cm;
+        i = right ? l + 1 : l;
+    }
+    h[i * kKnnThreads] = c;
 }
 
-template <int DP, int KC>
-__global__ void __launch_bounds__(128) k_knn(KnnArgs a)
+template <int DP>
+__global__ void __launch_bounds__(kKnnThreads) k_knn(KnnArgs a)
 {
     constexpr int NV = (DP + 1 + 3) / 4;
     constexpr int NS = (4 + 2 * DP + 3) / 4;
-    __shared__ __align__(16) float stage_x[4][DP][32];
-    __shared__ int stage_id[4][32];
+    __shared__ __align__(16) float stage_x[kKnnThreads / 32][DP][32];
+    __shared__ int stage_id[kKnnThreads / 32][32];
+    extern __shared__ unsigned long long heap_mem[];   // [k][kKnnThreads]
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const long long g0 = ((long long)blockIdx.x * 4 + warp) * 32;
+    const long long g0 = ((long long)blockIdx.x * (kKnnThreads / 32) + warp) * 32;
     if (g0 >= a.m) return;
     const long long pos = g0 + lane;
     const bool valid = pos < a.m;
@@ -78,9 +91,11 @@ __global__ void __launch_bounds__(128) k_knn(KnnArgs a)
         finite &= (__float_as_uint(q[k]) & 0x7f800000u) != 0x7f800000u;
     }
     if (!finite) atomicOr(a.err, kErrNonfinite);
-    unsigned long long s[KC];
-#pragma unroll
-    for (int i = 0; i < KC; i++) s[i] = (valid && i >= KC - a.k) ? kKeyEmpty : 0ull;
+    const int K = a.k;
+    unsigned long long* h = heap_mem + threadIdx.x;
+    for (int i = 0; i < K; i++) h[i * kKnnThreads] = kKeyEmpty;
+    // k-th best key so far (the heap root); invalid lanes never accept anything
+    unsigned long long kth = valid ? kKeyEmpty : 0ull;
 
     float (*sx)[32] = stage_x[warp];
     int* sid = stage_id[warp];
@@ -91,6 +106,10 @@ __global__ void __launch_bounds__(128) k_knn(KnnArgs a)
     // guarantees termination (with an error flag) should a node table be corrupt.
     long long budget = 2LL * a.num_nodes + 8;
     int vnodes = 0, vpts = 0;
+    // diagnostics: inner nodes, leaf chunks, lanes=queries chunks, transposed
+    // broadcasts, insertion-loop rounds, candidates, insertions
+    unsigned st[7] = {0, 0, 0, 0, 0, 0, 0};
+    const bool stats = a.stats != nullptr;
     while (sp > 0) {
         if (--budget < 0 || (unsigned)stack[sp - 1] >= (unsigned)a.num_nodes) {
             if (lane == 0) atomicOr(a.err, kErrInternal);
@@ -114,7 +133,7 @@ __global__ void __launch_bounds__(128) k_knn(KnnArgs a)
             const float g = fmaxf(fmaxf(__fsub_rn(f[4 + k], q[k]), __fsub_rn(q[k], f[4 + DP + k])), 0.0f);
             bnd = __fadd_rn(bnd, __fmul_rn(g, g));
         }
-        const float kd = __uint_as_float((unsigned)(s[KC - 1] >> 32));
+        const float kd = __uint_as_float((unsigned)(kth >> 32));
         const bool need = valid && !(bnd > kd);
         const unsigned needm = __ballot_sync(kFull, need);
         if (!needm) continue;
@@ -152,7 +171,9 @@ __global__ void __launch_bounds__(128) k_knn(KnnArgs a)
                 __syncwarp();
                 if (need) vpts += c;
                 unsigned cand = 0;
+                if (stats) st[1]++;
                 if (__popc(needm) > a.transpose_max) {
+                    if (stats) st[2]++;
                     // every lane scans all 32 staged points (sentinels beyond c)
 #pragma unroll
                     for (int j = 0; j < 32; j += 4) {
@@ -178,6 +199,7 @@ __global__ void __launch_bounds__(128) k_knn(KnnArgs a)
 #pragma unroll
                     for (int k = 0; k < DP; k++) px[k] = sx[k][lane];
                     unsigned rem = needm;
+                    if (stats) st[3] += __popc(needm);
                     while (rem) {
                         const int L = __ffs(rem) - 1;
                         rem &= rem - 1;
@@ -192,6 +214,10 @@ __global__ void __launch_bounds__(128) k_knn(KnnArgs a)
                         if (lane == L) cand = bits;
                     }
                 }
+                if (stats) {
+                    st[4] += __reduce_max_sync(kFull, (unsigned)__popc(cand));
+                    st[5] += __popc(cand);
+                }
                 // exact insertion of this lane's candidates
                 while (cand) {
                     const int j = __ffs(cand) - 1;
@@ -204,10 +230,15 @@ __global__ void __launch_bounds__(128) k_knn(KnnArgs a)
                     }
                     const unsigned long long key =
                         ((unsigned long long)__float_as_uint(acc) << 32) | (unsigned)sid[j];
-                    if (key < s[KC - 1]) topk_insert<KC>(s, key);
+                    if (key < kth) {
+                        heap_replace_root(h, K, key);
+                        kth = h[0];
+                        if (stats) st[6]++;
+                    }
                 }
             }
         } else {
+            if (stats) st[0]++;
             const int dim = (int)(meta & kMetaDimMask);
             const float sv = f[2];
             float qd = 0.0f;
@@ -224,20 +255,28 @@ __global__ void __launch_bounds__(128) k_knn(KnnArgs a)
             stack[sp++] = h0 + (right_near ? 1 : 0);   // near child last
         }
     }
+    if (stats) {
+        // st[0..4] are warp-uniform (counted once per warp); 5, 6 are per lane
+        st[5] = __reduce_add_sync(kFull, st[5]);
+        st[6] = __reduce_add_sync(kFull, st[6]);
+        if (lane == 0) {
+            atomicAdd(&a.stats[0], 1ull);
+            for (int i = 0; i < 7; i++) atomicAdd(&a.stats[1 + i], (unsigned long long)st[i]);
+        }
+    }
     if (a.visits && valid) {
         a.visits[2LL * qi] = vnodes;
         a.visits[2LL * qi + 1] = vpts;
     }
     if (valid) {
-        int* oi = a.ids + (long long)qi * a.k;
-        float* od = a.d2 + (long long)qi * a.k;
-#pragma unroll
-        for (int i = 0; i < KC; i++) {
-            const int j = i - (KC - a.k);
-            if (j >= 0) {
-                oi[j] = (int)(unsigned)(s[i] & 0xffffffffull);
-                od[j] = __uint_as_float((unsigned)(s[i] >> 32));
-            }
+        // empty the heap in descending order into positions k-1 .. 0
+        int* oi = a.ids + (long long)qi * K;
+        float* od = a.d2 + (long long)qi * K;
+        for (int sz = K; sz > 0; sz--) {
+            const unsigned long long top = h[0];
+            oi[sz - 1] = (int)(unsigned)(top & 0xffffffffull);
+            od[sz - 1] = __uint_as_float((unsigned)(top >> 32));
+            if (sz > 1) heap_replace_root(h, sz - 1, h[(sz - 1) * kKnnThreads]);
         }
     }
 }

@@ -21,6 +21,7 @@ struct panda_tree {
     float4* nodes = nullptr;  // [node_cap][ns]
     int64_t node_cap = 0;
     int64_t num_nodes = 0, num_leaves = 0;
+    int64_t node_slots = 0;   // records in use in the node table (holes included)
     int32_t depth = 0;
     float root_lo[16] = {0}, root_hi[16] = {0};
 };
@@ -74,7 +75,8 @@ panda_status build_tree(const float* points, int64_t n, int32_t d, int32_t bucke
                         cudaStream_t stream, panda_tree** out);
 panda_status knn_query(const panda_tree* t, const float* queries, int64_t m, int32_t k,
                        int32_t* ids, float* d2, const panda_query_params* params,
-                       cudaStream_t stream, unsigned* host_err, int32_t* visits = nullptr);
+                       cudaStream_t stream, unsigned* host_err, int32_t* visits = nullptr,
+                       unsigned long long* stats = nullptr);
 
 }  // namespace panda
 

@@ -30,7 +30,7 @@ SIGNATURES = {
     "panda_knn": ([_P, _P, _I64, _I32, _P, _P], ctypes.c_int),
     "panda_knn_async": ([_P, _P, _I64, _I32, _P, _P, _P, _P], ctypes.c_int),
     "panda_knn_host": ([_P, _P, _I64, _I32, _P, _P, _P, _P], ctypes.c_int),
-    "panda_knn_visits": ([_P, _P, _I64, _I32, _P, _P, _P, _P, _P], ctypes.c_int),
+    "panda_knn_visits": ([_P, _P, _I64, _I32, _P, _P, _P, _P, _P, _P], ctypes.c_int),
     "panda_free": ([_P], None),
     "panda_tree_get_info": ([_P, _P], ctypes.c_int),
     "panda_tree_copy": ([_P, _P, _P], ctypes.c_int),
@@ -58,7 +58,7 @@ class TreeInfo(ctypes.Structure):
                 ("num_nodes", ctypes.c_int64), ("num_leaves", ctypes.c_int64),
                 ("depth", ctypes.c_int32), ("node_floats", ctypes.c_int32),
                 ("point_floats", ctypes.c_int32), ("subtree_threshold", ctypes.c_int32),
-                ("device_bytes", ctypes.c_int64)]
+                ("device_bytes", ctypes.c_int64), ("node_slots", ctypes.c_int64)]
 
 
 _lib = None
@@ -130,7 +130,7 @@ class Tree:
     def raw(self):
         """(nodes [num_nodes][node_floats] float32, points [n][point_floats] float32) on the host."""
         inf = self.info()
-        nodes = np.empty((inf["num_nodes"], inf["node_floats"]), np.float32)
+        nodes = np.empty((inf["node_slots"], inf["node_floats"]), np.float32)
         pts = np.empty((inf["n"], inf["point_floats"]), np.float32)
         _check(_lib.panda_tree_copy(self._h, nodes.ctypes.data_as(ctypes.c_void_p),
                                     pts.ctypes.data_as(ctypes.c_void_p)))
@@ -239,8 +239,9 @@ def knn(tree: Tree, queries, k: int, order: str = "leaf", stream=None, out=None,
     return ids, d2
 
 
-def knn_visits(tree: Tree, queries, k: int, order: str = "leaf", stream=None):
-    """KNN plus per-query work counts [m][2] (nodes needed, bucket points scanned)."""
+def knn_visits(tree: Tree, queries, k: int, order: str = "leaf", stream=None, transpose_max: int = 0):
+    """KNN plus per-query work counts [m][2] (nodes needed, bucket points scanned)
+    and the traversal's event counters (dict)."""
     torch = _torch()
     L = load()
     q = _as_device_points(queries, "queries")
@@ -248,11 +249,15 @@ def knn_visits(tree: Tree, queries, k: int, order: str = "leaf", stream=None):
     ids = torch.empty((m, k), dtype=torch.int32, device=q.device)
     d2 = torch.empty((m, k), dtype=torch.float32, device=q.device)
     vis = torch.zeros((m, 2), dtype=torch.int32, device=q.device)
-    prm = QueryParams(ORDER[order], 0)
+    stats = torch.zeros(8, dtype=torch.int64, device=q.device)
+    prm = QueryParams(ORDER[order], int(transpose_max))
     _check(L.panda_knn_visits(tree.handle, ctypes.c_void_p(q.data_ptr()), m, int(k),
                               ctypes.c_void_p(ids.data_ptr()), ctypes.c_void_p(d2.data_ptr()),
-                              ctypes.c_void_p(vis.data_ptr()), ctypes.byref(prm), _stream_ptr(stream)))
-    return ids, d2, vis
+                              ctypes.c_void_p(vis.data_ptr()), ctypes.c_void_p(stats.data_ptr()),
+                              ctypes.byref(prm), _stream_ptr(stream)))
+    names = ["warps", "inner_nodes", "bucket_chunks", "lanes_query_chunks", "transposed_broadcasts",
+             "insert_rounds", "candidates", "insertions"]
+    return ids, d2, vis, dict(zip(names, stats.cpu().tolist()))
 
 
 def knn_sync(tree: Tree, queries, k: int):
