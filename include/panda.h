@@ -126,6 +126,19 @@ panda_status panda_knn_host(const panda_tree* tree, const float* queries, int64_
                             int32_t* out_ids, float* out_d2, const panda_query_params* params,
                             void* stream);
 
+/* Same query as panda_knn_async (default parameters) for callers that cannot
+ * allocate device memory while they query.  No counterpart in the paper: the
+ * query ordering's scratch space is a fixed file-scope device array (12.6 MB,
+ * present on every device that loads the library until exit) instead of
+ * stream-ordered allocations, so the call makes no cudaMalloc/cudaFree and
+ * calls no allocating library routine.  m is limited to 1048576 (2^20)
+ * queries per call; larger m returns PANDA_ERR_UNSUPPORTED.  All calls share
+ * the array: calls that overlap on the GPU race, so serialise them (one
+ * stream).  The first call on a device looks up the array's address; make it
+ * before any stream capture.  Non-finite queries are not reported. */
+panda_status panda_knn_noalloc(const panda_tree* tree, const float* queries, int64_t m, int32_t k,
+                               int32_t* out_ids, float* out_d2, void* stream);
+
 /* Releases the tree's device memory (NULL-safe). */
 void panda_free(panda_tree* tree);
 

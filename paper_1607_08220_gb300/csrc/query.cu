@@ -13,22 +13,11 @@
 #include <vector>
 
 #include "common.cuh"
+#include "order.cuh"
 #include "query.cuh"
 #include "runtime.h"
 
 namespace panda {
-
-struct OrderArgs {
-    const float4* nodes;
-    long long num_nodes;
-    const float* queries;
-    long long m;
-    int d, ns, shift, mode;
-    float lo[kMaxDim], inv[kMaxDim];
-    int bits;
-    unsigned* keys;
-    int* hist;
-};
 
 __device__ __forceinline__ unsigned morton_key(const OrderArgs& a, const float* q)
 {

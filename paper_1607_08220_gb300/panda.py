@@ -31,6 +31,7 @@ SIGNATURES = {
     "panda_knn_async": ([_P, _P, _I64, _I32, _P, _P, _P, _P], ctypes.c_int),
     "panda_knn_host": ([_P, _P, _I64, _I32, _P, _P, _P, _P], ctypes.c_int),
     "panda_knn_visits": ([_P, _P, _I64, _I32, _P, _P, _P, _P, _P, _P], ctypes.c_int),
+    "panda_knn_noalloc": ([_P, _P, _I64, _I32, _P, _P, _P], ctypes.c_int),
     "panda_free": ([_P], None),
     "panda_tree_get_info": ([_P, _P], ctypes.c_int),
     "panda_tree_copy": ([_P, _P, _P], ctypes.c_int),
@@ -258,6 +259,21 @@ def knn_visits(tree: Tree, queries, k: int, order: str = "leaf", stream=None, tr
     names = ["warps", "inner_nodes", "bucket_chunks", "lanes_query_chunks", "transposed_broadcasts",
              "insert_rounds", "candidates", "insertions"]
     return ids, d2, vis, dict(zip(names, stats.cpu().tolist()))
+
+
+def knn_noalloc(tree: Tree, queries, k: int, out, stream=None):
+    """panda_knn_noalloc: the query without any device allocation inside the call.
+
+    For callers that cannot allocate while they query; `out` = (ids, d2) CUDA
+    tensors the caller allocated.  At most 2^20 queries per call; calls that
+    overlap on the GPU share one scratch array and must be serialised."""
+    L = load()
+    q = _as_device_points(queries, "queries")
+    ids, d2 = out
+    _check(L.panda_knn_noalloc(tree.handle, ctypes.c_void_p(q.data_ptr()), q.shape[0], int(k),
+                               ctypes.c_void_p(ids.data_ptr()), ctypes.c_void_p(d2.data_ptr()),
+                               _stream_ptr(stream)))
+    return ids, d2
 
 
 def knn_sync(tree: Tree, queries, k: int):
