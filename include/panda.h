@@ -142,6 +142,37 @@ panda_status panda_knn_noalloc(const panda_tree* tree, const float* queries, int
 /* Releases the tree's device memory (NULL-safe). */
 void panda_free(panda_tree* tree);
 
+/* ---- batched form: many independent point sets, Sec. III-B (query batching) ---
+ * A batch owns device buffers for nsets sets of fixed sizes: all points
+ * (set s = rows point_off[s] .. point_off[s+1]-1 of a [sum n_points][d]
+ * array), all queries (likewise), and the outputs (set s's [n_queries][k]
+ * block starts at out_off[s] elements).  panda_batch_run enqueues, with no host
+ * synchronisation, one build of every set's kd-tree (a forest) and the exact
+ * KNN of every set's queries against its own tree; the first run captures the
+ * sequence in a CUDA graph, later runs replay it (write new inputs into the
+ * same buffers between runs).  Ids in the outputs are row indices within the
+ * set.  panda_batch_status reports the last run's errors once `stream` has
+ * passed it (it synchronises `stream`). */
+typedef struct panda_batch panda_batch;
+typedef struct panda_set_desc {
+    int64_t n_points;   /* >= 1 */
+    int64_t n_queries;  /* >= 0 */
+    int32_t k;          /* 1 .. 64 */
+    int32_t reserved;
+} panda_set_desc;
+panda_status panda_batch_create(const panda_set_desc* sets, int32_t nsets, int32_t d, int32_t bucket,
+                                panda_batch** out);
+panda_status panda_batch_buffers(panda_batch* batch, float** points, float** queries, int32_t** out_ids,
+                                 float** out_d2);
+/* point_off, query_off, out_off: host arrays of nsets + 1 entries (each may be NULL). */
+panda_status panda_batch_offsets(const panda_batch* batch, int64_t* point_off, int64_t* query_off,
+                                 int64_t* out_off);
+panda_status panda_batch_run(panda_batch* batch, void* stream);
+panda_status panda_batch_status(panda_batch* batch, void* stream);
+/* Forest statistics of the last run; *kernels_per_run = kernels in the captured graph. */
+panda_status panda_batch_info(const panda_batch* batch, panda_tree_info* info, int64_t* kernels_per_run);
+void panda_batch_free(panda_batch* batch);
+
 /* ---- inspection -------------------------------------------------------------
  * panda_tree_get_info fills *info.  panda_tree_copy copies the tree's node
  * table ([node_slots][node_floats] floats) and packed points

@@ -18,6 +18,7 @@ namespace {
 thread_local char g_err[512] = "";
 thread_local int64_t g_launches = 0;
 bool g_timing = false;
+thread_local bool g_timing_suppressed = false;
 
 struct PhaseRow {
     const char* name;
@@ -57,8 +58,9 @@ panda_status note_launch(const char* what)
 
 int64_t launches_so_far() { return g_launches; }
 bool phase_timing_enabled() { return g_timing; }
+void set_phase_timing_suppressed(bool on) { g_timing_suppressed = on; }
 
-PhaseTimer::PhaseTimer(cudaStream_t s) : stream_(s), on_(g_timing) {}
+PhaseTimer::PhaseTimer(cudaStream_t s) : stream_(s), on_(g_timing && !g_timing_suppressed) {}
 
 PhaseTimer::~PhaseTimer()
 {

@@ -27,6 +27,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <vector>
 
 #include "common.cuh"
@@ -61,6 +62,8 @@ struct BuildArgs {
     int lvl_stride;
     int* cnt;
     unsigned* err;
+    const int* set_off;   // forest: [nsets + 1] point offsets of independent sets (null: one tree)
+    int nsets;
     float4* nodes;
     long long node_cap;
     int ns;
@@ -160,31 +163,75 @@ __device__ void block_plan_tiles(BuildArgs& a, int x, int A)
     }
 }
 
+// Roots: one tree (node 0) or, for a forest, node s for set s.  Roots with
+// more than T points start the level stage; the others go straight to the
+// subtree stage.
 __global__ void k_init(BuildArgs a)
 {
-    if (a.n > a.T) {
-        if (threadIdx.x == 0) {
-            Active r;
-            r.start = 0;
-            r.count = a.n;
-            r.node = 0;
-            r.depth = 0;
-            a.act[0][0] = r;
-            a.cnt[kCntActive0] = 1;
-            a.cnt[kCntNodes] = 1;
+    __shared__ int sh[33];
+    __shared__ int s_act, s_small;
+    const int nsets = a.set_off ? a.nsets : 1;
+    if (threadIdx.x == 0) {
+        s_act = 0;
+        s_small = 0;
+    }
+    __syncthreads();
+    for (int c0 = 0; c0 < nsets; c0 += blockDim.x) {
+        const int si = c0 + threadIdx.x;
+        int start = 0, count = 0;
+        if (si < nsets) {
+            start = a.set_off ? a.set_off[si] : 0;
+            count = a.set_off ? a.set_off[si + 1] - start : a.n;
+        }
+        const int act = (si < nsets && count > a.T) ? 1 : 0;
+        const int sml = (si < nsets && !act) ? 1 : 0;
+        int ta, ts;
+        const int pa = block_excl_scan(act, sh, &ta) + s_act;
+        const int ps = block_excl_scan(sml, sh, &ts) + s_small;
+        if (act) {
+            if (pa < a.act_cap) {
+                Active r;
+                r.start = start;
+                r.count = count;
+                r.node = si;
+                r.depth = 0;
+                a.act[0][pa] = r;
+            } else {
+                atomicOr(a.err, kErrActiveOverflow);
+            }
+        } else if (sml) {
+            if (ps < a.small_cap) {
+                Small sm;
+                sm.start = start;
+                sm.count = count;
+                sm.node = si;
+                sm.depth_parity = 0;
+                a.small[ps] = sm;
+            } else {
+                atomicOr(a.err, kErrSmallOverflow);
+            }
         }
         __syncthreads();
-        block_plan_tiles(a, 0, 1);
-    } else if (threadIdx.x == 0) {
-        Small s;
-        s.start = 0;
-        s.count = a.n;
-        s.node = 0;
-        s.depth_parity = 0;
-        a.small[0] = s;
-        a.cnt[kCntSmall] = 1;
-        a.cnt[kCntNodes] = 1;
+        if (threadIdx.x == 0) {
+            s_act += ta;
+            s_small += ts;
+        }
+        __syncthreads();
     }
+    if (threadIdx.x == 0) {
+        a.cnt[kCntActive0] = min(s_act, a.act_cap);
+        a.cnt[kCntSmall] = s_small;
+        a.cnt[kCntNodes] = nsets;
+    }
+    __syncthreads();
+    block_plan_tiles(a, 0, min(s_act, a.act_cap));
+}
+
+// After a fixed number of level passes (graph-captured builds): nodes still
+// active would have needed more passes; report it instead of building them.
+__global__ void k_check_levels(BuildArgs a, int L)
+{
+    if (threadIdx.x == 0 && a.cnt[kCntActive0 + (L & 1)] > 0) atomicOr(a.err, kErrLevels);
 }
 
 // ------------------------------------------------------------------ A2 + A3
@@ -1095,33 +1142,33 @@ struct Plan {
     long long node_cap;
 };
 
-panda_status build_once(const float* points, int n, int d, int bucket, cudaStream_t stream,
-                        const Plan& pl, panda_tree* t, int* need_small, long long* need_nodes,
-                        unsigned* err_out)
-{
-    PhaseTimer timer(stream);
-    Buffers ws(stream);
+}  // namespace
+
+// Build workspace: device buffers of one build (or of a reusable forest plan).
+struct BuildState {
     BuildArgs a;
-    memset(&a, 0, sizeof(a));
-    a.n = n;
-    a.d = d;
-    a.dp = t->dp;
-    a.bucket = bucket;
-    a.T = pl.T;
-    a.n_pad = (n + 3) & ~3;
-    a.in = points;
-    a.act_cap = pl.act_cap;
-    a.tile_cap = pl.tile_cap;
-    a.small_cap = pl.small_cap;
-    a.lvl_stride = pl.lvl_stride;
-    a.node_cap = pl.node_cap;
-    a.ns = t->ns;
-    a.nv = t->nv;
-    a.nodes = t->nodes;
-    a.pts = t->points;
+    Plan pl;
+    std::vector<void*> bufs;
+    int max_set = 0;   // largest tree (sets the number of level passes)
+};
+
+namespace {
+
+panda_status build_alloc(BuildState& S, int n, int d, cudaStream_t stream)
+{
+    BuildArgs& a = S.a;
+    const Plan& pl = S.pl;
     panda_status st;
+    auto get = [&](auto** ptr, size_t count, const char* what) -> panda_status {
+        void* p = nullptr;
+        panda_status r = ws_alloc(&p, std::max<size_t>(count, 1) * sizeof(**ptr), stream, what);
+        if (r != PANDA_OK) return r;
+        S.bufs.push_back(p);
+        *ptr = static_cast<std::remove_reference_t<decltype(*ptr)>>(p);
+        return PANDA_OK;
+    };
 #define GET(ptr, count, what) \
-    if ((st = ws.get(&(ptr), (count), what)) != PANDA_OK) return st
+    if ((st = get(&(ptr), (count), what)) != PANDA_OK) return st
     const size_t np = (size_t)a.n_pad;
     for (int p = 0; p < 2; p++) {
         GET(a.X[p], np * d, "coordinate buffers");
@@ -1146,54 +1193,143 @@ panda_status build_once(const float* points, int n, int d, int bucket, cudaStrea
     GET(a.cnt, (size_t)kCntSlots, "counters");
     GET(a.err, (size_t)1, "error word");
 #undef GET
+    return PANDA_OK;
+}
+
+void build_release(BuildState& S, cudaStream_t stream)
+{
+    for (void* p : S.bufs) ws_free(p, stream);
+    S.bufs.clear();
+}
+
+void init_args(BuildState& S, const float* points, int n, int d, int bucket, const panda_tree* t)
+{
+    BuildArgs& a = S.a;
+    const Plan& pl = S.pl;
+    a.n = n;
+    a.d = d;
+    a.dp = t->dp;
+    a.bucket = bucket;
+    a.T = pl.T;
+    a.n_pad = (n + 3) & ~3;
+    a.in = points;
+    a.act_cap = pl.act_cap;
+    a.tile_cap = pl.tile_cap;
+    a.small_cap = pl.small_cap;
+    a.lvl_stride = pl.lvl_stride;
+    a.node_cap = pl.node_cap;
+    a.ns = t->ns;
+    a.nv = t->nv;
+    a.nodes = t->nodes;
+    a.pts = t->points;
+}
+
+// Clear counters, transpose the points and seed the roots.
+panda_status enqueue_start(BuildState& S, cudaStream_t stream, PhaseTimer& timer)
+{
+    BuildArgs& a = S.a;
     PANDA_CUDA(cudaMemsetAsync(a.cnt, 0, kCntSlots * sizeof(int), stream), "clear counters");
     PANDA_CUDA(cudaMemsetAsync(a.err, 0, sizeof(unsigned), stream), "clear error word");
-    PANDA_CUDA(cudaMemsetAsync(a.lvl_count, 0, pl.max_levels * sizeof(int), stream), "clear levels");
-
+    PANDA_CUDA(cudaMemsetAsync(a.lvl_count, 0, S.pl.max_levels * sizeof(int), stream), "clear levels");
     const int sms = num_sms();
     timer.begin("transpose");
-    {
-        int blocks = (int)std::min<long long>((a.n_pad + 255) / 256, (long long)sms * 16);
-        k_transpose<<<blocks, 256, 0, stream>>>(a);
-        PANDA_LAUNCHED("k_transpose");
-        k_init<<<1, 1024, 0, stream>>>(a);
-        PANDA_LAUNCHED("k_init");
+    int blocks = (int)std::min<long long>((a.n_pad + 255) / 256, (long long)sms * 16);
+    k_transpose<<<blocks, 256, 0, stream>>>(a);
+    PANDA_LAUNCHED("k_transpose");
+    k_init<<<1, 1024, 0, stream>>>(a);
+    PANDA_LAUNCHED("k_init");
+    return PANDA_OK;
+}
+
+// The six kernels of one data-parallel level pass.
+panda_status enqueue_level(BuildState& S, int L, cudaStream_t stream, PhaseTimer& timer)
+{
+    BuildArgs& a = S.a;
+    const Plan& pl = S.pl;
+    const int d = a.d;
+    const int acap = (int)std::min<long long>(L < 30 ? (1LL << L) * std::max(1, a.set_off ? a.nsets : 1)
+                                                     : (1LL << 30), pl.act_cap);
+    const int tcap = (int)std::min<long long>(pl.tile_cap, (long long)a.n / kTile + 2LL * acap + 2);
+    timer.begin("level.sample");
+    k_sample<<<acap, 256, d * kSamples * 4, stream>>>(a, L);
+    PANDA_LAUNCHED("k_sample");
+    timer.begin("level.hist");
+    k_hist<<<tcap, 256, 0, stream>>>(a, L);
+    PANDA_LAUNCHED("k_hist");
+    timer.begin("level.select");
+    k_select<<<acap, 256, 0, stream>>>(a, L);
+    PANDA_LAUNCHED("k_select");
+    k_tilecount<<<(tcap + 7) / 8, 256, 0, stream>>>(a, L);
+    PANDA_LAUNCHED("k_tilecount");
+    k_children<<<1, 1024, 0, stream>>>(a, L);
+    PANDA_LAUNCHED("k_children");
+    timer.begin("level.partition");
+    k_partition<<<tcap, 256, 0, stream>>>(a, L);
+    PANDA_LAUNCHED("k_partition");
+    return PANDA_OK;
+}
+
+// Subtree stage and the level-stage boxes.
+panda_status enqueue_finish(BuildState& S, int nlevels, cudaStream_t stream, PhaseTimer& timer)
+{
+    BuildArgs& a = S.a;
+    const int sms = num_sms();
+    timer.begin("subtree");
+    const int wb = (int)warp_bytes(a.d, S.pl.T);
+    const int wpb = std::max(1, std::min(8, (227 * 1024) / wb));
+    k_subtree<<<sms, wpb * 32, (size_t)wpb * wb, stream>>>(a, wb);
+    PANDA_LAUNCHED("k_subtree");
+    timer.begin("boxes");
+    if (nlevels > 0) {
+        k_boxes<<<1, 1024, 0, stream>>>(a, nlevels);
+        PANDA_LAUNCHED("k_boxes");
     }
-    auto launch_level = [&](int L) -> panda_status {
-        const int acap = (int)std::min<long long>(L < 30 ? (1LL << L) : (1LL << 30), pl.act_cap);
-        const int tcap = (int)std::min<long long>(pl.tile_cap, (long long)n / kTile + 2LL * acap + 2);
-        timer.begin("level.sample");
-        k_sample<<<acap, 256, d * kSamples * 4, stream>>>(a, L);
-        PANDA_LAUNCHED("k_sample");
-        timer.begin("level.hist");
-        k_hist<<<tcap, 256, 0, stream>>>(a, L);
-        PANDA_LAUNCHED("k_hist");
-        timer.begin("level.select");
-        k_select<<<acap, 256, 0, stream>>>(a, L);
-        PANDA_LAUNCHED("k_select");
-        k_tilecount<<<(tcap + 7) / 8, 256, 0, stream>>>(a, L);
-        PANDA_LAUNCHED("k_tilecount");
-        k_children<<<1, 1024, 0, stream>>>(a, L);
-        PANDA_LAUNCHED("k_children");
-        timer.begin("level.partition");
-        k_partition<<<tcap, 256, 0, stream>>>(a, L);
-        PANDA_LAUNCHED("k_partition");
-        return PANDA_OK;
-    };
+    timer.end();
+    return PANDA_OK;
+}
+
+int levels_for(int max_set, int T)
+{
+    if (max_set <= T) return 0;
+    return (int)ceil(log2((double)max_set / T)) + 2;
+}
+
+void set_tree_counts(panda_tree* t, const int* hc, long long level_ids, long long n_small)
+{
+    // ids below level_ids belong to the level stage (subtree roots included,
+    // which the subtree stage counts again); the rest of the table may hold holes
+    t->node_slots = hc[kCntNodes];
+    t->num_nodes = level_ids + hc[kCntRealNodes] - n_small;
+    t->num_leaves = hc[kCntLeaves];
+    t->depth = hc[kCntDepth];
+}
+
+panda_status build_once(const float* points, int n, int d, int bucket, cudaStream_t stream,
+                        const Plan& pl, panda_tree* t, int* need_small, long long* need_nodes,
+                        unsigned* err_out)
+{
+    PhaseTimer timer(stream);
+    BuildState S;
+    memset(&S.a, 0, sizeof(S.a));
+    S.pl = pl;
+    init_args(S, points, n, d, bucket, t);
+    struct Release {
+        BuildState& s;
+        cudaStream_t st;
+        ~Release() { build_release(s, st); }
+    } release{S, stream};
+    panda_status st = build_alloc(S, n, d, stream);
+    if (st != PANDA_OK) return st;
+    if ((st = enqueue_start(S, stream, timer)) != PANDA_OK) return st;
     int L = 0;
-    int levels_est = 0;
-    if (n > pl.T) {
-        double r = (double)n / pl.T;
-        levels_est = (int)ceil(log2(r)) + 2;
-    }
-    levels_est = std::min(levels_est, pl.max_levels);
+    const int levels_est = std::min(levels_for(n, pl.T), pl.max_levels);
     for (; L < levels_est; L++)
-        if ((st = launch_level(L)) != PANDA_OK) return st;
+        if ((st = enqueue_level(S, L, stream, timer)) != PANDA_OK) return st;
     int hc[kCntSlots];
     unsigned herr = 0;
     for (;;) {
-        PANDA_CUDA(cudaMemcpyAsync(hc, a.cnt, sizeof(hc), cudaMemcpyDeviceToHost, stream), "read counters");
-        PANDA_CUDA(cudaMemcpyAsync(&herr, a.err, sizeof(herr), cudaMemcpyDeviceToHost, stream), "read error");
+        PANDA_CUDA(cudaMemcpyAsync(hc, S.a.cnt, sizeof(hc), cudaMemcpyDeviceToHost, stream), "read counters");
+        PANDA_CUDA(cudaMemcpyAsync(&herr, S.a.err, sizeof(herr), cudaMemcpyDeviceToHost, stream), "read error");
         PANDA_CUDA(cudaStreamSynchronize(stream), "level stage");
         if (herr) break;
         if (hc[kCntActive0 + (L & 1)] == 0) break;
@@ -1201,7 +1337,7 @@ panda_status build_once(const float* points, int n, int d, int bucket, cudaStrea
             herr |= kErrDepth;
             break;
         }
-        if ((st = launch_level(L)) != PANDA_OK) return st;
+        if ((st = enqueue_level(S, L, stream, timer)) != PANDA_OK) return st;
         L++;
     }
     *need_small = hc[kCntSmall];
@@ -1209,36 +1345,147 @@ panda_status build_once(const float* points, int n, int d, int bucket, cudaStrea
     if (herr) return PANDA_OK;   // caller decides (retry or error)
     const int nlevels = hc[kCntLevels];
     const long long level_ids = hc[kCntNodes], n_small = hc[kCntSmall];
-
-    timer.begin("subtree");
-    {
-        const int wb = (int)warp_bytes(d, pl.T);
-        int wpb = std::max(1, std::min(8, (227 * 1024) / wb));
-        k_subtree<<<sms, wpb * 32, (size_t)wpb * wb, stream>>>(a, wb);
-        PANDA_LAUNCHED("k_subtree");
-    }
-    timer.begin("boxes");
-    if (nlevels > 0) {
-        k_boxes<<<1, 1024, 0, stream>>>(a, nlevels);
-        PANDA_LAUNCHED("k_boxes");
-    }
-    timer.end();
-    PANDA_CUDA(cudaMemcpyAsync(hc, a.cnt, sizeof(hc), cudaMemcpyDeviceToHost, stream), "read counters");
-    PANDA_CUDA(cudaMemcpyAsync(&herr, a.err, sizeof(herr), cudaMemcpyDeviceToHost, stream), "read error");
+    if ((st = enqueue_finish(S, nlevels, stream, timer)) != PANDA_OK) return st;
+    PANDA_CUDA(cudaMemcpyAsync(hc, S.a.cnt, sizeof(hc), cudaMemcpyDeviceToHost, stream), "read counters");
+    PANDA_CUDA(cudaMemcpyAsync(&herr, S.a.err, sizeof(herr), cudaMemcpyDeviceToHost, stream), "read error");
     PANDA_CUDA(cudaStreamSynchronize(stream), "subtree stage");
     timer.finish();
     *need_nodes = hc[kCntNodes];
     *err_out = herr;
-    // ids below level_ids belong to the level stage (subtree roots included,
-    // which the subtree stage counts again); the rest of the table may hold holes
-    t->node_slots = hc[kCntNodes];
-    t->num_nodes = level_ids + hc[kCntRealNodes] - n_small;
-    t->num_leaves = hc[kCntLeaves];
-    t->depth = hc[kCntDepth];
+    set_tree_counts(t, hc, level_ids, n_small);
     return PANDA_OK;
 }
 
 }  // namespace
+
+// ------------------------------------------------------------------ forests
+
+// A forest of independent trees over the concatenated point sets (set s =
+// rows [set_off[s], set_off[s+1])): root of set s is node s.  Its buffers are
+// allocated once; forest_enqueue then launches a fixed number of level passes
+// (enough for the largest set plus two) with no host synchronisation, so the
+// whole build can be captured in a CUDA graph; running out of passes is
+// reported through the error word (kErrLevels).
+panda_status forest_create(const long long* set_sizes, int nsets, int d, int bucket, const float* points,
+                           cudaStream_t stream, panda_tree* t, BuildState** out)
+{
+    *out = nullptr;
+    if (nsets < 1 || d < 1 || d > kMaxDim || bucket < 1 || bucket > kMaxBucket) {
+        set_error("forest: invalid sets, d or bucket");
+        return PANDA_ERR_INVALID_ARGUMENT;
+    }
+    long long n = 0;
+    int max_set = 0;
+    std::vector<int> off(nsets + 1, 0);
+    for (int s = 0; s < nsets; s++) {
+        if (set_sizes[s] < 1) {
+            set_error("forest: set %d is empty", s);
+            return PANDA_ERR_INVALID_ARGUMENT;
+        }
+        off[s] = (int)n;
+        n += set_sizes[s];
+        max_set = std::max<long long>(max_set, set_sizes[s]);
+        if (n >= (1LL << 31) - 4) {
+            set_error("forest: more than 2^31 points in total");
+            return PANDA_ERR_UNSUPPORTED;
+        }
+    }
+    off[nsets] = (int)n;
+    panda_status st = configure_kernels();
+    if (st != PANDA_OK) return st;
+    cudaGetDevice(&t->device);
+    t->n = n;
+    t->d = d;
+    t->dp = padded_dim(d);
+    t->bucket = bucket;
+    t->nv = point_float4s(t->dp);
+    t->ns = node_float4s(t->dp);
+    BuildState* S = new BuildState();
+    memset(&S->a, 0, sizeof(S->a));
+    Plan& pl = S->pl;
+    pl.T = subtree_threshold(d, bucket);
+    t->threshold = pl.T;
+    pl.act_cap = (int)(n / (pl.T + 1)) + 1;
+    pl.tile_cap = (int)(n / kTile) + 2 * pl.act_cap + 4;
+    pl.small_cap = nsets + 8 * pl.act_cap + 64;
+    pl.lvl_stride = pl.act_cap;
+    pl.max_levels = kMaxDepth + 1;
+    pl.node_cap = 2LL * n + 8 + nsets + (long long)num_sms() * 8 * kIdChunk;
+    S->max_set = max_set;
+    t->node_cap = pl.node_cap;
+    void *pn = nullptr, *pp = nullptr, *po = nullptr;
+    st = ws_alloc(&pn, (size_t)pl.node_cap * t->ns * sizeof(float4), stream, "forest nodes");
+    if (st == PANDA_OK) st = ws_alloc(&pp, (size_t)n * t->nv * sizeof(float4), stream, "forest points");
+    if (st == PANDA_OK) st = ws_alloc(&po, (size_t)(nsets + 1) * sizeof(int), stream, "forest set offsets");
+    if (st != PANDA_OK) {
+        ws_free(pn, stream);
+        ws_free(pp, stream);
+        ws_free(po, stream);
+        delete S;
+        return st;
+    }
+    t->nodes = static_cast<float4*>(pn);
+    t->points = static_cast<float4*>(pp);
+    S->bufs.push_back(po);
+    init_args(*S, points, (int)n, d, bucket, t);
+    S->a.set_off = static_cast<const int*>(po);
+    S->a.nsets = nsets;
+    cudaError_t e = cudaMemcpyAsync(po, off.data(), (nsets + 1) * sizeof(int), cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) st = cuda_fail(e, "forest: set offsets");
+    if (st == PANDA_OK) st = build_alloc(*S, (int)n, d, stream);
+    if (st != PANDA_OK) {
+        build_release(*S, stream);
+        ws_free(pn, stream);
+        ws_free(pp, stream);
+        t->nodes = nullptr;
+        t->points = nullptr;
+        delete S;
+        return st;
+    }
+    *out = S;
+    return PANDA_OK;
+}
+
+int forest_levels(const BuildState* S) { return std::min(levels_for(S->max_set, S->pl.T) + 2, S->pl.max_levels); }
+
+panda_status forest_enqueue(BuildState* S, cudaStream_t stream)
+{
+    PhaseTimer timer(stream);
+    panda_status st = enqueue_start(*S, stream, timer);
+    if (st != PANDA_OK) return st;
+    const int L = forest_levels(S);
+    for (int l = 0; l < L; l++)
+        if ((st = enqueue_level(*S, l, stream, timer)) != PANDA_OK) return st;
+    k_check_levels<<<1, 32, 0, stream>>>(S->a, L);
+    PANDA_LAUNCHED("k_check_levels");
+    return enqueue_finish(*S, L, stream, timer);
+}
+
+// After the stream has passed a forest build: its error word and node counts.
+panda_status forest_collect(BuildState* S, panda_tree* t, unsigned* err, cudaStream_t stream)
+{
+    int hc[kCntSlots];
+    PANDA_CUDA(cudaMemcpyAsync(hc, S->a.cnt, sizeof(hc), cudaMemcpyDeviceToHost, stream), "forest counters");
+    PANDA_CUDA(cudaMemcpyAsync(err, S->a.err, sizeof(unsigned), cudaMemcpyDeviceToHost, stream), "forest error");
+    PANDA_CUDA(cudaStreamSynchronize(stream), "forest collect");
+    // level-stage ids: roots plus two per split; subtree roots are counted twice
+    long long level_ids = 0;
+    int lc[kMaxDepth + 1];
+    PANDA_CUDA(cudaMemcpy(lc, S->a.lvl_count, sizeof(int) * S->pl.max_levels, cudaMemcpyDeviceToHost),
+               "forest level counts");
+    level_ids = S->a.nsets;
+    for (int l = 0; l < S->pl.max_levels; l++) level_ids += 2LL * lc[l];
+    set_tree_counts(t, hc, level_ids, hc[kCntSmall]);
+    return PANDA_OK;
+}
+
+void forest_destroy(BuildState* S, cudaStream_t stream)
+{
+    if (!S) return;
+    build_release(*S, stream);
+    delete S;
+}
 
 panda_status build_tree(const float* points, int64_t n64, int32_t d, int32_t bucket, cudaStream_t stream,
                         panda_tree** out)

@@ -29,6 +29,7 @@ enum : unsigned {
     kErrActiveOverflow = 16u,
     kErrTileOverflow = 32u,
     kErrInternal = 64u,
+    kErrLevels = 128u,   // a graph-captured build ran out of level passes
 };
 
 // Split modes of a node.

@@ -9,7 +9,7 @@
 namespace panda {
 
 template <int DP>
-panda_status launch_knn_dp(const KnnArgs& a, cudaStream_t s)
+panda_status configure_knn()
 {
     static bool configured = false;
     if (!configured) {
@@ -18,8 +18,20 @@ panda_status launch_knn_dp(const KnnArgs& a, cudaStream_t s)
                    "configure k_knn");
         configured = true;
     }
+    return PANDA_OK;
+}
+
+template <int DP>
+panda_status launch_knn_dp(const KnnArgs& a, cudaStream_t s)
+{
+    panda_status st = configure_knn<DP>();
+    if (st != PANDA_OK) return st;
+    // one launch per tree: one warp per 32 queries; many sets: persistent
+    // warps (8 blocks per SM) draining the job queue
     const long long warps = (a.m + 31) / 32;
-    const long long blocks = (warps + kKnnThreads / 32 - 1) / (kKnnThreads / 32);
+    const long long blocks = a.jobs ? (long long)num_sms() * 8
+                                    : (warps + kKnnThreads / 32 - 1) / (kKnnThreads / 32);
+    if (blocks <= 0) return PANDA_OK;
     const size_t heap_bytes = (size_t)a.k * kKnnThreads * 8;
     k_knn<DP><<<(unsigned)blocks, kKnnThreads, heap_bytes, s>>>(a);
     PANDA_LAUNCHED("k_knn");

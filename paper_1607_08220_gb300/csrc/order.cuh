@@ -17,6 +17,13 @@ struct OrderArgs {
     int bits;
     unsigned* keys;
     int* hist;
+    // several query sets, each against its own root of one forest (null: one tree):
+    // query rows [qset_off[s], qset_off[s+1]) belong to set s, whose root is node s,
+    // whose points start at set_poff[s] and whose bins start at set_bin[s]
+    const int* qset_off;
+    const int* set_poff;
+    const int* set_bin;
+    int nsets;
 };
 
 // key of every query (leaf bucket or Morton code >> shift) and its histogram

@@ -44,7 +44,16 @@ __global__ void k_order_keys(OrderArgs a)
     if (a.mode == PANDA_ORDER_MORTON) {
         key = morton_key(a, q) >> a.shift;
     } else {
-        int node = 0;
+        int node = 0, set = 0;
+        if (a.qset_off) {
+            int lo = 0, hi = a.nsets - 1;        // last set whose first row <= i
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (a.qset_off[mid] <= i) lo = mid; else hi = mid - 1;
+            }
+            set = lo;
+            node = set;
+        }
         for (int step = 0; step <= kMaxDepth + 1; step++) {
             if ((unsigned)node >= (unsigned)a.num_nodes) {
                 node = 0;
@@ -61,7 +70,8 @@ __global__ void k_order_keys(OrderArgs a)
             }
         }
         const int4 h = __ldg(reinterpret_cast<const int4*>(a.nodes + (long long)node * a.ns));
-        key = (unsigned)h.x >> a.shift;
+        key = a.qset_off ? (unsigned)a.set_bin[set] + ((unsigned)(h.x - a.set_poff[set]) >> a.shift)
+                         : (unsigned)h.x >> a.shift;
     }
     a.keys[i] = key;
     atomicAdd(&a.hist[key], 1);
@@ -243,6 +253,7 @@ panda_status knn_query(const panda_tree* t, const float* queries, int64_t m, int
     }
     timer.begin("query.traverse");
     KnnArgs ka;
+    memset(&ka, 0, sizeof(ka));
     ka.nodes = t->nodes;
     ka.pts = t->points;
     ka.queries = queries;

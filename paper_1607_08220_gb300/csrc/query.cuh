@@ -29,7 +29,31 @@
 
 namespace panda {
 
+// One query set against one tree (a request of the served form, or one set of
+// a batched forest).  Rows of `queries` are the set's queries; `perm` (may be
+// null) lists them in traversal order as row_base + row; ids written are
+// stored ids - id_base.
+struct KnnSet {
+    const float4* nodes;
+    const float4* pts;
+    long long num_nodes, npts;
+    const float* queries;
+    const int* perm;
+    int* ids;
+    float* d2;
+    long long m;
+    int root, id_base, k, row_base;
+};
+// A warp job: traversal positions [pos, pos + 32) of one set.
+struct KnnJob {
+    int set, pos;
+};
+
 struct KnnArgs {
+    const KnnSet* sets;   // multi-set launch (with jobs); null for the single-tree fields below
+    const KnnJob* jobs;
+    int njobs;
+    int* job_head;        // device work-queue head (persistent warps take jobs from it)
     const float4* nodes;
     const float4* pts;
     const float* queries;
@@ -68,55 +92,49 @@ __device__ __forceinline__ void heap_replace_root(unsigned long long* h, int k, 
     h[i * kKnnThreads] = c;
 }
 
+// Traversal of one warp job: positions [g0, g0 + 32) of set S.
 template <int DP>
-__global__ void __launch_bounds__(kKnnThreads) k_knn(KnnArgs a)
+__device__ __forceinline__ void knn_warp_job(const KnnArgs& a, const KnnSet& S, long long g0,
+                                             float (*sx)[32], int* sid, unsigned long long* h)
 {
     constexpr int NV = (DP + 1 + 3) / 4;
     constexpr int NS = (4 + 2 * DP + 3) / 4;
-    __shared__ __align__(16) float stage_x[kKnnThreads / 32][DP][32];
-    __shared__ int stage_id[kKnnThreads / 32][32];
-    extern __shared__ unsigned long long heap_mem[];   // [k][kKnnThreads]
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const long long g0 = ((long long)blockIdx.x * (kKnnThreads / 32) + warp) * 32;
-    if (g0 >= a.m) return;
+    const int lane = threadIdx.x & 31;
     const long long pos = g0 + lane;
-    const bool valid = pos < a.m;
+    const bool valid = pos < S.m;
     int qi = 0;
-    if (valid) qi = a.perm ? a.perm[pos] : (int)pos;
+    if (valid) qi = S.perm ? S.perm[pos] - S.row_base : (int)pos;
     float q[DP];
     bool finite = true;
 #pragma unroll
     for (int k = 0; k < DP; k++) {
-        q[k] = (valid && k < a.d) ? a.queries[(long long)qi * a.d + k] : 0.0f;
+        q[k] = (valid && k < a.d) ? S.queries[(long long)qi * a.d + k] : 0.0f;
         finite &= (__float_as_uint(q[k]) & 0x7f800000u) != 0x7f800000u;
     }
     if (!finite) atomicOr(a.err, kErrNonfinite);
-    const int K = a.k;
-    unsigned long long* h = heap_mem + threadIdx.x;
+    const int K = S.k;
     for (int i = 0; i < K; i++) h[i * kKnnThreads] = kKeyEmpty;
     // k-th best key so far (the heap root); invalid lanes never accept anything
     unsigned long long kth = valid ? kKeyEmpty : 0ull;
 
-    float (*sx)[32] = stage_x[warp];
-    int* sid = stage_id[warp];
     int stack[kMaxDepth + 4];
     int sp = 0;
-    stack[sp++] = 0;
+    stack[sp++] = S.root;
     // A valid tree is visited in at most 2 * num_nodes pops; the cap only
     // guarantees termination (with an error flag) should a node table be corrupt.
-    long long budget = 2LL * a.num_nodes + 8;
+    long long budget = 2LL * S.num_nodes + 8;
     int vnodes = 0, vpts = 0;
     // diagnostics: inner nodes, leaf chunks, lanes=queries chunks, transposed
     // broadcasts, insertion-loop rounds, candidates, insertions
     unsigned st[7] = {0, 0, 0, 0, 0, 0, 0};
     const bool stats = a.stats != nullptr;
     while (sp > 0) {
-        if (--budget < 0 || (unsigned)stack[sp - 1] >= (unsigned)a.num_nodes) {
+        if (--budget < 0 || (unsigned)stack[sp - 1] >= (unsigned)S.num_nodes) {
             if (lane == 0) atomicOr(a.err, kErrInternal);
             break;
         }
         const int node = stack[--sp];
-        const float4* rec = a.nodes + (long long)node * NS;
+        const float4* rec = S.nodes + (long long)node * NS;
         float f[4 * NS];
 #pragma unroll
         for (int r = 0; r < NS; r++) {
@@ -142,7 +160,7 @@ __global__ void __launch_bounds__(kKnnThreads) k_knn(KnnArgs a)
         const int h1 = __float_as_int(f[1]);
         const unsigned meta = __float_as_uint(f[3]);
         if (meta & kMetaLeaf) {
-            if (h0 < 0 || h1 < 0 || (long long)h0 + h1 > a.npts) {
+            if (h0 < 0 || h1 < 0 || (long long)h0 + h1 > S.npts) {
                 if (lane == 0) atomicOr(a.err, kErrInternal);
                 break;
             }
@@ -150,7 +168,7 @@ __global__ void __launch_bounds__(kKnnThreads) k_knn(KnnArgs a)
                 const int c = min(32, h1 - b0);
                 __syncwarp();
                 if (lane < c) {
-                    const float4* src = a.pts + (long long)(h0 + b0 + lane) * NV;
+                    const float4* src = S.pts + (long long)(h0 + b0 + lane) * NV;
 #pragma unroll
                     for (int v = 0; v < NV; v++) {
                         const float4 p = __ldg(src + v);
@@ -270,14 +288,58 @@ __global__ void __launch_bounds__(kKnnThreads) k_knn(KnnArgs a)
     }
     if (valid) {
         // empty the heap in descending order into positions k-1 .. 0
-        int* oi = a.ids + (long long)qi * K;
-        float* od = a.d2 + (long long)qi * K;
+        int* oi = S.ids + (long long)qi * K;
+        float* od = S.d2 + (long long)qi * K;
         for (int sz = K; sz > 0; sz--) {
             const unsigned long long top = h[0];
-            oi[sz - 1] = (int)(unsigned)(top & 0xffffffffull);
+            const int id = (int)(unsigned)(top & 0xffffffffull);
+            oi[sz - 1] = id < 0 ? id : id - S.id_base;
             od[sz - 1] = __uint_as_float((unsigned)(top >> 32));
             if (sz > 1) heap_replace_root(h, sz - 1, h[(sz - 1) * kKnnThreads]);
         }
+    }
+}
+
+
+template <int DP>
+__global__ void __launch_bounds__(kKnnThreads) k_knn(KnnArgs a)
+{
+    __shared__ __align__(16) float stage_x[kKnnThreads / 32][DP][32];
+    __shared__ int stage_id[kKnnThreads / 32][32];
+    extern __shared__ unsigned long long heap_mem[];   // [kmax][kKnnThreads]
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    unsigned long long* h = heap_mem + threadIdx.x;
+    if (!a.jobs) {
+        // one tree: warp w takes positions [32 w, 32 w + 32)
+        KnnSet S;
+        S.nodes = a.nodes;
+        S.pts = a.pts;
+        S.num_nodes = a.num_nodes;
+        S.npts = a.npts;
+        S.queries = a.queries;
+        S.perm = a.perm;
+        S.ids = a.ids;
+        S.d2 = a.d2;
+        S.m = a.m;
+        S.root = 0;
+        S.id_base = 0;
+        S.row_base = 0;
+        S.k = a.k;
+        const long long g0 = ((long long)blockIdx.x * (kKnnThreads / 32) + warp) * 32;
+        if (g0 >= a.m) return;
+        knn_warp_job<DP>(a, S, g0, stage_x[warp], stage_id[warp], h);
+        return;
+    }
+    // many sets: persistent warps take jobs from the device work queue
+    for (;;) {
+        int j = 0;
+        if (lane == 0) j = atomicAdd(a.job_head, 1);
+        j = __shfl_sync(kFull, j, 0);
+        if (j >= a.njobs) break;
+        const KnnJob jb = a.jobs[j];
+        const KnnSet S = a.sets[jb.set];
+        knn_warp_job<DP>(a, S, jb.pos, stage_x[warp], stage_id[warp], h);
+        __syncwarp();
     }
 }
 

@@ -55,6 +55,11 @@ struct PhaseTimer {
 };
 
 bool phase_timing_enabled();
+// While set on this thread, PhaseTimers record nothing (used around graph capture).
+void set_phase_timing_suppressed(bool on);
+// Launch attributes of the traversal kernels (set before any graph capture).
+panda_status configure_knn_lo();
+panda_status configure_knn_hi();
 int64_t launches_so_far();
 
 // Convert a CUDA error into a status with a message.
@@ -77,6 +82,15 @@ panda_status knn_query(const panda_tree* t, const float* queries, int64_t m, int
                        int32_t* ids, float* d2, const panda_query_params* params,
                        cudaStream_t stream, unsigned* host_err, int32_t* visits = nullptr,
                        unsigned long long* stats = nullptr);
+
+// Forests of independent trees (batched form), in build.cu.
+struct BuildState;
+panda_status forest_create(const long long* set_sizes, int nsets, int d, int bucket, const float* points,
+                           cudaStream_t stream, panda_tree* t, BuildState** out);
+panda_status forest_enqueue(BuildState* S, cudaStream_t stream);
+panda_status forest_collect(BuildState* S, panda_tree* t, unsigned* err, cudaStream_t stream);
+void forest_destroy(BuildState* S, cudaStream_t stream);
+int forest_levels(const BuildState* S);
 
 }  // namespace panda
 

@@ -32,6 +32,13 @@ SIGNATURES = {
     "panda_knn_host": ([_P, _P, _I64, _I32, _P, _P, _P, _P], ctypes.c_int),
     "panda_knn_visits": ([_P, _P, _I64, _I32, _P, _P, _P, _P, _P, _P], ctypes.c_int),
     "panda_knn_noalloc": ([_P, _P, _I64, _I32, _P, _P, _P], ctypes.c_int),
+    "panda_batch_create": ([_P, _I32, _I32, _I32, ctypes.POINTER(_P)], ctypes.c_int),
+    "panda_batch_buffers": ([_P, _P, _P, _P, _P], ctypes.c_int),
+    "panda_batch_offsets": ([_P, _P, _P, _P], ctypes.c_int),
+    "panda_batch_run": ([_P, _P], ctypes.c_int),
+    "panda_batch_status": ([_P, _P], ctypes.c_int),
+    "panda_batch_info": ([_P, _P, _P], ctypes.c_int),
+    "panda_batch_free": ([_P], None),
     "panda_free": ([_P], None),
     "panda_tree_get_info": ([_P, _P], ctypes.c_int),
     "panda_tree_copy": ([_P, _P, _P], ctypes.c_int),
@@ -195,6 +202,80 @@ def canonical_from_raw(nodes: np.ndarray, pts: np.ndarray, d: int) -> dict:
                 split=split_col[order].copy(), start=start, count=count, left=left, right=right,
                 lo=nodes[order, 4:4 + d].copy(), hi=nodes[order, 4 + dp:4 + dp + d].copy(),
                 perm=ids)
+
+
+class SetDesc(ctypes.Structure):
+    _fields_ = [("n_points", ctypes.c_int64), ("n_queries", ctypes.c_int64), ("k", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class _DeviceArray:
+    """Zero-copy view of library-owned device memory (CUDA array interface)."""
+
+    def __init__(self, ptr: int, shape, typestr: str):
+        self.__cuda_array_interface__ = {"shape": tuple(int(x) for x in shape), "typestr": typestr,
+                                         "data": (int(ptr), False), "version": 3, "strides": None}
+
+
+class Batch:
+    """Batched form: many independent point sets built and queried in one graph launch."""
+
+    def __init__(self, n_points, n_queries, ks, d: int, bucket: int = 32):
+        torch = _torch()
+        L = load()
+        ns = len(n_points)
+        descs = (SetDesc * ns)(*[SetDesc(int(a), int(b), int(c), 0) for a, b, c in zip(n_points, n_queries, ks)])
+        h = ctypes.c_void_p()
+        _check(L.panda_batch_create(descs, ns, int(d), int(bucket), ctypes.byref(h)))
+        self._h = h
+        self.nsets, self.d = ns, d
+        self.ks = [int(k) for k in ks]
+        po = (ctypes.c_int64 * (ns + 1))()
+        qo = (ctypes.c_int64 * (ns + 1))()
+        oo = (ctypes.c_int64 * (ns + 1))()
+        _check(L.panda_batch_offsets(h, po, qo, oo))
+        self.point_off, self.query_off, self.out_off = list(po), list(qo), list(oo)
+        pp, qp, ip, dp = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
+        _check(L.panda_batch_buffers(h, ctypes.byref(pp), ctypes.byref(qp), ctypes.byref(ip), ctypes.byref(dp)))
+        dev = torch.device("cuda", torch.cuda.current_device())
+        self.points = torch.as_tensor(_DeviceArray(pp.value, (self.point_off[-1], d), "<f4"), device=dev)
+        self.queries = torch.as_tensor(_DeviceArray(qp.value, (max(self.query_off[-1], 1), d), "<f4"),
+                                       device=dev)[:self.query_off[-1]]
+        self.ids = torch.as_tensor(_DeviceArray(ip.value, (max(self.out_off[-1], 1),), "<i4"),
+                                   device=dev)[:self.out_off[-1]]
+        self.d2 = torch.as_tensor(_DeviceArray(dp.value, (max(self.out_off[-1], 1),), "<f4"),
+                                  device=dev)[:self.out_off[-1]]
+
+    def run(self, stream=None):
+        _check(load().panda_batch_run(self._h, _stream_ptr(stream)))
+
+    def status(self, stream=None):
+        _check(load().panda_batch_status(self._h, _stream_ptr(stream)))
+
+    def result(self, s: int):
+        """(ids, d2) of set s as [n_queries][k] views of the output buffers."""
+        a, b = self.out_off[s], self.out_off[s + 1]
+        k = self.ks[s]
+        return self.ids[a:b].view(-1, k), self.d2[a:b].view(-1, k)
+
+    def info(self):
+        inf = TreeInfo()
+        kr = ctypes.c_int64()
+        _check(load().panda_batch_info(self._h, ctypes.byref(inf), ctypes.byref(kr)))
+        out = {f: getattr(inf, f) for f, _ in TreeInfo._fields_}
+        out["kernels_per_run"] = kr.value
+        return out
+
+    def free(self):
+        if getattr(self, "_h", None):
+            load().panda_batch_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
 
 
 def _as_device_points(x, what: str):
