@@ -41,8 +41,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["cosmology_self", "uniform_small", "features_10d"],
+    ap.add_argument("--workload", choices=["cosmology_self", "uniform_small", "features_10d", "batched_sets"],
                     default="cosmology_self")
+    ap.add_argument("--nsets", type=int, default=512, help="sets of the batched workload")
     ap.add_argument("--order", choices=["leaf", "morton", "none"], default="leaf")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -410,10 +411,96 @@ def run_ours(args):
     return 0
 
 
+def run_batched(args):
+    """Batched form: all sets built and queried by one captured graph, against the
+    plain path (one panda_build + panda_knn per set, serialised on one stream)."""
+    import torch
+
+    import paper_1607_08220_gb300 as P
+    from paper_1607_08220_gb300 import build_ext, workloads
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    build_ext.build()
+    P.load()
+    t0 = time.time()
+    sets = workloads.batched_sets(nsets=args.nsets)
+    gen_s = time.time() - t0
+    npts = [p.shape[0] for p, _, _ in sets]
+    nq = [q.shape[0] for _, q, _ in sets]
+    ks = [k for _, _, k in sets]
+    m_total = sum(nq)
+    batch = P.Batch(npts, nq, ks, d=3, bucket=32)
+    for s_, (pts, q, k) in enumerate(sets):
+        batch.points[batch.point_off[s_]:batch.point_off[s_ + 1]].copy_(torch.from_numpy(pts))
+        batch.queries[batch.query_off[s_]:batch.query_off[s_ + 1]].copy_(torch.from_numpy(q))
+    stream = torch.cuda.current_stream()
+    for _ in range(max(3, args.warmup)):
+        batch.run()
+    torch.cuda.synchronize()
+    batch.status()
+    cvd = os.environ.get("CUDA_VISIBLE_DEVICES")
+    clocks = ClockSampler(cvd.split(",")[0].strip() if cvd else "0")
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        batch.run()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    batch.status()
+    b_ms = e0.elapsed_time(e1) / args.steps
+    # plain path on the same device data: one build + one query per set
+    pts_d = [batch.points[batch.point_off[i]:batch.point_off[i + 1]] for i in range(len(sets))]
+    q_d = [batch.queries[batch.query_off[i]:batch.query_off[i + 1]] for i in range(len(sets))]
+    outs = [(torch.empty((nq[i], ks[i]), dtype=torch.int32, device="cuda"),
+             torch.empty((nq[i], ks[i]), dtype=torch.float32, device="cuda")) for i in range(len(sets))]
+
+    def plain_step():
+        for i in range(len(sets)):
+            t = P.build(pts_d[i], 32)
+            if nq[i]:
+                P.knn(t, q_d[i], ks[i], out=outs[i])
+            t.free()
+
+    plain_step()
+    torch.cuda.synchronize()
+    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    psteps = max(1, min(args.steps, 3))
+    p0.record(stream)
+    for _ in range(psteps):
+        plain_step()
+    p1.record(stream)
+    torch.cuda.synchronize()
+    p_ms = p0.elapsed_time(p1) / psteps
+    same = all(torch.equal(outs[i][0], batch.result(i)[0]) and
+               torch.equal(outs[i][1].view(torch.int32), batch.result(i)[1].view(torch.int32))
+               for i in range(len(sets)) if nq[i])
+    info = batch.info()
+    line = {"metric": METRIC + " [batched form]", "value": m_total / (b_ms / 1e3), "unit": UNIT,
+            "n_gpus": 1, "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": b_ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": f"batched_sets: {len(sets)} sets, sizes log-uniform [1e3, 2e6], "
+                                   f"{sum(npts)} points, {m_total} queries, k in {{4,8,16,32}}, B=32",
+                       "sets": len(sets), "points": int(sum(npts)), "queries": int(m_total),
+                       "step": "build every set's tree + answer every set's queries (one graph launch)",
+                       "l2": "inputs larger than L2"},
+            "clocks": clk, "gpu_launches": int(info["kernels_per_run"]) * args.steps,
+            "plain": {"value": m_total / (p_ms / 1e3), "ms_per_step": p_ms,
+                      "path": "one panda_build + one panda_knn per set, serialised on one stream"},
+            "speedup_vs_plain": p_ms / b_ms, "identical_to_plain": bool(same),
+            "build_pts_per_s": sum(npts) / (b_ms / 1e3), "generation_s": gen_s}
+    print(json.dumps(line), flush=True)
+    batch.free()
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batched_sets":
+        return run_batched(args)
     return run_ours(args)
 
 
