@@ -173,6 +173,36 @@ panda_status panda_batch_status(panda_batch* batch, void* stream);
 panda_status panda_batch_info(const panda_batch* batch, panda_tree_info* info, int64_t* kernels_per_run);
 void panda_batch_free(panda_batch* batch);
 
+/* ---- served form: resident trees, continuous batching (Sec. III-B pipelining) --
+ * A server keeps trees resident and answers KNN requests asynchronously.  A
+ * scheduler thread takes queued requests in arrival order -- any tree, size
+ * and k (1..64) -- into batches of at most max_batch_queries queries (a larger
+ * request runs alone) and runs each batch as one query-ordering pass and one
+ * persistent traversal launch; up to two batches are in flight, so requests
+ * arriving while one runs join the next.  Results equal panda_knn's.
+ * panda_server_add_tree builds on the server's own stream (queries continue)
+ * and is refused with PANDA_ERR_OUT_OF_MEMORY if mem_budget_bytes (0 = no
+ * budget) or the device's free memory cannot hold it.  Requests reference
+ * caller-owned device buffers, which must stay valid until the request is
+ * done.  Times are nanoseconds since the server was created. */
+typedef struct panda_server panda_server;
+panda_status panda_server_create(int64_t mem_budget_bytes, int64_t max_batch_queries, panda_server** out);
+panda_status panda_server_add_tree(panda_server* server, const float* points, int64_t n, int32_t d,
+                                   int32_t bucket, int32_t* tree_id);
+panda_status panda_server_submit(panda_server* server, int32_t tree_id, const float* queries, int64_t m,
+                                 int32_t k, int32_t* out_ids, float* out_d2, int64_t* request_id);
+/* *done = 1 once the request finished; returns the request's status. */
+panda_status panda_server_poll(panda_server* server, int64_t request_id, int32_t* done);
+/* Waits at most timeout_us; PANDA_ERR_TIMEOUT if the request is not done by then. */
+panda_status panda_server_wait(panda_server* server, int64_t request_id, int64_t timeout_us);
+panda_status panda_server_request_info(panda_server* server, int64_t request_id, int64_t* t_submit_ns,
+                                       int64_t* t_done_ns, int64_t* batch_id);
+int64_t panda_server_now_ns(panda_server* server);
+panda_status panda_server_stats(panda_server* server, int64_t* batches, int64_t* requests, int64_t* pending,
+                                int64_t* bytes_used);
+/* Finishes queued and running requests, then releases every tree and the server. */
+void panda_server_destroy(panda_server* server);
+
 /* ---- inspection -------------------------------------------------------------
  * panda_tree_get_info fills *info.  panda_tree_copy copies the tree's node
  * table ([node_slots][node_floats] floats) and packed points

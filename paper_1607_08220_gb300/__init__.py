@@ -5,8 +5,8 @@ The compute path is the CUDA library ``_lib/libpanda.so`` behind the C ABI in
 ``include/panda.h``; :mod:`.panda` is its Python binding.  Build the library
 with :func:`paper_1607_08220_gb300.build_ext.build`.
 """
-from .panda import (Batch, PandaError, Tree, build, build_host, kernel_launches, knn, knn_host, knn_sync, knn_visits,
+from .panda import (Batch, PandaError, Server, Tree, build, build_host, kernel_launches, knn, knn_host, knn_sync, knn_visits,
                     load, phase_times, set_phase_timing, version)
 
-__all__ = ["Batch", "PandaError", "Tree", "build", "build_host", "knn", "knn_host", "knn_sync", "knn_visits", "load",
+__all__ = ["Batch", "PandaError", "Server", "Tree", "build", "build_host", "knn", "knn_host", "knn_sync", "knn_visits", "load",
            "phase_times", "set_phase_timing", "kernel_launches", "version"]

@@ -1,0 +1,537 @@
+// serve.cu -- served form: resident trees and continuous batching of KNN
+// requests (the paper pipelines query batches across stages, Sec. III-B).
+//
+// Trees stay resident in device memory; a tree is admitted only if the
+// server's memory budget and the device's free memory hold it, and it is
+// built on its own stream so queries keep running.  A scheduler thread forms
+// batches from the request queue in arrival order -- requests of different
+// trees, sizes and k -- and runs each batch as one ordering pass (one counting
+// sort over all its queries, each request keyed by the leaves of its own
+// tree) and one persistent traversal launch whose warps take (request, 32
+// queries) jobs from a device work queue.  Up to two batches are in flight:
+// requests that arrive while one runs join the next as soon as a slot frees.
+// Each request records its submit and completion times.
+#include <string.h>
+
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "order.cuh"
+#include "query.cuh"
+#include "runtime.h"
+
+namespace panda {
+template <int DP>
+panda_status launch_knn_dp(const KnnArgs& a, cudaStream_t s);
+
+// Ordering of one request of a served batch against its own tree.
+struct OrderSet {
+    const float4* nodes;
+    long long num_nodes;
+    const float* queries;
+    int root, bin_base, shift, ns, row_begin, d;
+};
+
+// Keys of all queries of a batch: row i belongs to the request whose rows start
+// at row_begin[s] <= i; key = the request's first bin + (leaf start >> shift).
+__global__ void k_order_keys_multi(const OrderSet* sets, const int* row_begin, int nsets, long long m,
+                                   unsigned* keys, int* hist)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    int lo = 0, hi = nsets - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (row_begin[mid] <= i) lo = mid; else hi = mid - 1;
+    }
+    const OrderSet S = sets[lo];
+    const float* q = S.queries + (i - S.row_begin) * S.d;
+    int node = S.root;
+    for (int step = 0; step <= kMaxDepth + 1; step++) {
+        if ((unsigned)node >= (unsigned)S.num_nodes) {
+            node = S.root;
+            break;
+        }
+        const int4 h = __ldg(reinterpret_cast<const int4*>(S.nodes + (long long)node * S.ns));
+        const unsigned meta = (unsigned)h.w;
+        if (meta & kMetaLeaf) break;
+        node = (meta & kMetaIndex) ? h.x : h.x + (q[meta & kMetaDimMask] >= __int_as_float(h.z) ? 1 : 0);
+    }
+    const int4 h = __ldg(reinterpret_cast<const int4*>(S.nodes + (long long)node * S.ns));
+    const unsigned key = (unsigned)S.bin_base + ((unsigned)h.x >> S.shift);
+    keys[i] = key;
+    atomicAdd(&hist[key], 1);
+}
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+struct Request {
+    int64_t id = 0;
+    int tree = 0;
+    const float* queries = nullptr;
+    int64_t m = 0;
+    int k = 0;
+    int32_t* ids = nullptr;
+    float* d2 = nullptr;
+    int64_t t_submit = 0, t_done = -1;
+    int64_t batch = -1;
+    panda_status status = PANDA_OK;
+    bool done = false;
+};
+
+struct InFlight {
+    int64_t batch_id = 0;
+    std::vector<int64_t> reqs;
+    cudaEvent_t done = nullptr;
+    std::vector<void*> scratch;
+};
+
+}  // namespace
+
+struct Server {
+    int device = 0;
+    int64_t budget = 0, used = 0;
+    int64_t max_batch_queries = 0;
+    int max_inflight = 2;
+    cudaStream_t qstream = nullptr, bstream = nullptr;
+    std::vector<panda_tree*> trees;
+    std::vector<int64_t> tree_bytes;
+    std::mutex mu;
+    std::condition_variable cv;
+    std::deque<int64_t> pending;
+    std::unordered_map<int64_t, Request> reqs;
+    std::vector<InFlight> inflight;
+    int64_t next_id = 1, next_batch = 0;
+    int64_t batches = 0, batched_requests = 0;
+    bool stop = false;
+    std::thread sched;
+    Clock::time_point t0;
+    std::mutex build_mu;
+
+    int64_t now_ns() const
+    {
+        return std::chrono::duration_cast<std::chrono::nanoseconds>(Clock::now() - t0).count();
+    }
+};
+
+namespace {
+
+panda_status enqueue_batch(Server* S, const std::vector<Request*>& batch, InFlight& fl)
+{
+    cudaStream_t s = S->qstream;
+    const int nr = (int)batch.size();
+    const panda_tree* t0 = S->trees[batch[0]->tree];
+    const int d = t0->d;
+    long long m_total = 0;
+    int kmax = 1;
+    std::vector<int> row_begin(nr + 1);
+    std::vector<OrderSet> os(nr);
+    std::vector<KnnSet> ks(nr);
+    std::vector<KnnJob> jobs;
+    long long bins = 0;
+    for (int r = 0; r < nr; r++) {
+        const Request* R = batch[r];
+        const panda_tree* t = S->trees[R->tree];
+        row_begin[r] = (int)m_total;
+        // bins of this request: about 4 per query, at most 2^20, no finer than a point
+        long long want = std::min<long long>(1LL << 20, std::max<long long>(64, 4 * R->m));
+        int sh = 0;
+        while ((t->n >> sh) + 1 > want) sh++;
+        OrderSet& o = os[r];
+        o.nodes = t->nodes;
+        o.num_nodes = t->node_slots;
+        o.queries = R->queries;
+        o.root = 0;
+        o.bin_base = (int)bins;
+        o.shift = sh;
+        o.ns = t->ns;
+        o.row_begin = (int)m_total;
+        o.d = d;
+        bins += (t->n >> sh) + 1;
+        KnnSet& K = ks[r];
+        memset(&K, 0, sizeof(K));
+        K.nodes = t->nodes;
+        K.pts = t->points;
+        K.num_nodes = t->node_slots;
+        K.npts = t->n;
+        K.queries = R->queries;
+        K.ids = R->ids;
+        K.d2 = R->d2;
+        K.m = R->m;
+        K.root = 0;
+        K.id_base = 0;
+        K.k = R->k;
+        K.row_base = (int)m_total;
+        for (long long p = 0; p < R->m; p += 32) jobs.push_back(KnnJob{r, (int)p});
+        m_total += R->m;
+        kmax = std::max(kmax, R->k);
+    }
+    row_begin[nr] = (int)m_total;
+    const int nb = (int)bins;
+    const int nblk = (nb + 4095) / 4096;
+    auto get = [&](void** p, size_t bytes, const char* what) -> panda_status {
+        panda_status st = ws_alloc(p, std::max<size_t>(bytes, 16), s, what);
+        if (st == PANDA_OK) fl.scratch.push_back(*p);
+        return st;
+    };
+    unsigned* keys;
+    int *perm, *hist, *bsum, *rb, *head;
+    unsigned* err;
+    OrderSet* d_os;
+    KnnSet* d_ks;
+    KnnJob* d_jobs;
+    panda_status st;
+    if ((st = get((void**)&keys, m_total * 4, "served keys")) != PANDA_OK) return st;
+    if ((st = get((void**)&perm, m_total * 4, "served permutation")) != PANDA_OK) return st;
+    if ((st = get((void**)&hist, (size_t)nblk * 4096 * 4, "served histogram")) != PANDA_OK) return st;
+    if ((st = get((void**)&bsum, (size_t)nblk * 4, "served block sums")) != PANDA_OK) return st;
+    if ((st = get((void**)&rb, (size_t)(nr + 1) * 4, "served row offsets")) != PANDA_OK) return st;
+    if ((st = get((void**)&head, 4, "served queue head")) != PANDA_OK) return st;
+    if ((st = get((void**)&err, 4, "served error word")) != PANDA_OK) return st;
+    if ((st = get((void**)&d_os, nr * sizeof(OrderSet), "served order sets")) != PANDA_OK) return st;
+    if ((st = get((void**)&d_ks, nr * sizeof(KnnSet), "served query sets")) != PANDA_OK) return st;
+    if ((st = get((void**)&d_jobs, std::max<size_t>(jobs.size(), 1) * sizeof(KnnJob), "served jobs")) != PANDA_OK)
+        return st;
+    for (int r = 0; r < nr; r++) ks[r].perm = perm + row_begin[r];
+    PANDA_CUDA(cudaMemcpyAsync(rb, row_begin.data(), (nr + 1) * 4, cudaMemcpyHostToDevice, s), "served copy");
+    PANDA_CUDA(cudaMemcpyAsync(d_os, os.data(), nr * sizeof(OrderSet), cudaMemcpyHostToDevice, s), "served copy");
+    PANDA_CUDA(cudaMemcpyAsync(d_ks, ks.data(), nr * sizeof(KnnSet), cudaMemcpyHostToDevice, s), "served copy");
+    if (!jobs.empty())
+        PANDA_CUDA(cudaMemcpyAsync(d_jobs, jobs.data(), jobs.size() * sizeof(KnnJob), cudaMemcpyHostToDevice, s),
+                   "served copy");
+    PANDA_CUDA(cudaMemsetAsync(hist, 0, (size_t)nb * 4, s), "served clear");
+    PANDA_CUDA(cudaMemsetAsync(head, 0, 4, s), "served clear");
+    PANDA_CUDA(cudaMemsetAsync(err, 0, 4, s), "served clear");
+    if (m_total > 0) {
+        const unsigned gb = (unsigned)((m_total + 255) / 256);
+        k_order_keys_multi<<<gb, 256, 0, s>>>(d_os, rb, nr, m_total, keys, hist);
+        PANDA_LAUNCHED("k_order_keys_multi");
+        k_scan_blocks<<<nblk, 1024, 0, s>>>(hist, nb, bsum);
+        PANDA_LAUNCHED("k_scan_blocks");
+        k_scan_sums<<<1, 1024, 0, s>>>(bsum, nblk);
+        PANDA_LAUNCHED("k_scan_sums");
+        k_order_scatter<<<gb, 256, 0, s>>>(keys, m_total, hist, bsum, perm);
+        PANDA_LAUNCHED("k_order_scatter");
+        KnnArgs ka;
+        memset(&ka, 0, sizeof(ka));
+        ka.sets = d_ks;
+        ka.jobs = d_jobs;
+        ka.njobs = (int)jobs.size();
+        ka.job_head = head;
+        ka.err = err;
+        ka.m = m_total;
+        ka.d = d;
+        ka.k = kmax;
+        ka.transpose_max = 12;
+        switch (t0->dp) {
+            case 2: st = launch_knn_dp<2>(ka, s); break;
+            case 3: st = launch_knn_dp<3>(ka, s); break;
+            case 4: st = launch_knn_dp<4>(ka, s); break;
+            case 8: st = launch_knn_dp<8>(ka, s); break;
+            case 10: st = launch_knn_dp<10>(ka, s); break;
+            default: st = launch_knn_dp<16>(ka, s); break;
+        }
+        if (st != PANDA_OK) return st;
+    }
+    PANDA_CUDA(cudaEventCreateWithFlags(&fl.done, cudaEventDisableTiming), "served event");
+    PANDA_CUDA(cudaEventRecord(fl.done, s), "served event");
+    return PANDA_OK;
+}
+
+void release(Server* S, InFlight& fl)
+{
+    for (void* p : fl.scratch) ws_free(p, S->qstream);
+    fl.scratch.clear();
+    if (fl.done) cudaEventDestroy(fl.done);
+    fl.done = nullptr;
+}
+
+void scheduler(Server* S)
+{
+    cudaSetDevice(S->device);
+    std::unique_lock<std::mutex> lk(S->mu);
+    for (;;) {
+        // completions
+        bool finished = false;
+        for (size_t i = 0; i < S->inflight.size();) {
+            InFlight& fl = S->inflight[i];
+            const cudaError_t q = cudaEventQuery(fl.done);
+            if (q == cudaErrorNotReady) {
+                i++;
+                continue;
+            }
+            const int64_t t = S->now_ns();
+            const panda_status st = q == cudaSuccess ? PANDA_OK : PANDA_ERR_CUDA;
+            for (int64_t id : fl.reqs) {
+                Request& R = S->reqs[id];
+                R.t_done = t;
+                R.status = st;
+                R.done = true;
+            }
+            release(S, fl);
+            S->inflight.erase(S->inflight.begin() + i);
+            finished = true;
+        }
+        if (finished) S->cv.notify_all();
+        if (S->stop && S->pending.empty() && S->inflight.empty()) break;
+        if (!S->pending.empty() && (int)S->inflight.size() < S->max_inflight) {
+            // next batch: requests in arrival order, same padded width, up to the query cap
+            std::vector<Request*> batch;
+            std::vector<int64_t> ids;
+            int64_t qsum = 0;
+            const int dp = S->trees[S->reqs[S->pending.front()].tree]->dp;
+            while (!S->pending.empty()) {
+                Request& R = S->reqs[S->pending.front()];
+                if (S->trees[R.tree]->dp != dp) break;
+                if (!batch.empty() && qsum + R.m > S->max_batch_queries) break;
+                batch.push_back(&R);
+                ids.push_back(R.id);
+                qsum += R.m;
+                S->pending.pop_front();
+            }
+            InFlight fl;
+            fl.batch_id = S->next_batch++;
+            fl.reqs = ids;
+            for (Request* R : batch) R->batch = fl.batch_id;
+            lk.unlock();
+            const panda_status st = enqueue_batch(S, batch, fl);
+            lk.lock();
+            S->batches++;
+            S->batched_requests += (int64_t)batch.size();
+            if (st != PANDA_OK) {
+                const int64_t t = S->now_ns();
+                release(S, fl);
+                for (int64_t id : ids) {
+                    Request& R = S->reqs[id];
+                    R.status = st;
+                    R.t_done = t;
+                    R.done = true;
+                }
+                S->cv.notify_all();
+            } else {
+                S->inflight.push_back(fl);
+            }
+            continue;
+        }
+        if (!S->inflight.empty())
+            S->cv.wait_for(lk, std::chrono::microseconds(20));
+        else
+            S->cv.wait(lk, [S] { return S->stop || !S->pending.empty(); });
+    }
+}
+
+}  // namespace
+}  // namespace panda
+
+struct panda_server : panda::Server {};
+
+using namespace panda;
+
+extern "C" {
+
+panda_status panda_server_create(int64_t mem_budget_bytes, int64_t max_batch_queries, panda_server** out)
+{
+    clear_error();
+    if (!out || mem_budget_bytes < 0 || max_batch_queries < 1) {
+        set_error("panda_server_create: invalid argument");
+        return PANDA_ERR_INVALID_ARGUMENT;
+    }
+    *out = nullptr;
+    panda_server* S = new panda_server();
+    cudaGetDevice(&S->device);
+    S->budget = mem_budget_bytes;
+    S->max_batch_queries = max_batch_queries;
+    S->t0 = Clock::now();
+    cudaError_t e = cudaStreamCreateWithFlags(&S->qstream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S->bstream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        delete S;
+        return cuda_fail(e, "panda_server_create: streams");
+    }
+    panda_status st = configure_knn_lo();
+    if (st == PANDA_OK) st = configure_knn_hi();
+    if (st != PANDA_OK) {
+        cudaStreamDestroy(S->qstream);
+        cudaStreamDestroy(S->bstream);
+        delete S;
+        return st;
+    }
+    S->sched = std::thread(scheduler, S);
+    *out = S;
+    return PANDA_OK;
+}
+
+panda_status panda_server_add_tree(panda_server* S, const float* points, int64_t n, int32_t d, int32_t bucket,
+                                   int32_t* tree_id)
+{
+    clear_error();
+    if (!S || !tree_id || !points || n < 1 || d < 1 || bucket < 1) {
+        set_error("panda_server_add_tree: invalid argument");
+        return PANDA_ERR_INVALID_ARGUMENT;
+    }
+    // admission: the resident tree plus the build's transient buffers must fit
+    const int dp = padded_dim(d);
+    const int64_t tree_est = n * point_float4s(dp) * 16 + (4 * n / bucket + 200000) * node_float4s(dp) * 16;
+    const int64_t build_est = n * (2LL * (4 * d + 4)) + tree_est;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        if (S->budget > 0 && S->used + tree_est > S->budget) {
+            set_error("panda_server_add_tree: memory budget of %lld bytes would be exceeded (%lld used, %lld needed)",
+                      (long long)S->budget, (long long)S->used, (long long)tree_est);
+            return PANDA_ERR_OUT_OF_MEMORY;
+        }
+    }
+    size_t free_b = 0, total_b = 0;
+    cudaMemGetInfo(&free_b, &total_b);
+    if ((int64_t)free_b < build_est) {
+        set_error("panda_server_add_tree: %zu bytes free on the device, about %lld needed", free_b,
+                  (long long)build_est);
+        return PANDA_ERR_OUT_OF_MEMORY;
+    }
+    std::lock_guard<std::mutex> blk(S->build_mu);   // one build at a time, on the build stream
+    panda_tree* t = nullptr;
+    panda_status st = build_tree(points, n, d, bucket, S->bstream, &t);
+    if (st != PANDA_OK) return st;
+    cudaError_t e = cudaStreamSynchronize(S->bstream);
+    if (e != cudaSuccess) {
+        panda_free(t);
+        return cuda_fail(e, "panda_server_add_tree: build");
+    }
+    const int64_t bytes = (int64_t)t->node_cap * t->ns * 16 + t->n * t->nv * 16;
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->trees.push_back(t);
+    S->tree_bytes.push_back(bytes);
+    S->used += bytes;
+    *tree_id = (int32_t)S->trees.size() - 1;
+    return PANDA_OK;
+}
+
+panda_status panda_server_submit(panda_server* S, int32_t tree_id, const float* queries, int64_t m, int32_t k,
+                                 int32_t* out_ids, float* out_d2, int64_t* request_id)
+{
+    clear_error();
+    if (!S || !request_id || m < 0 || k < 1 || (m > 0 && (!queries || !out_ids || !out_d2))) {
+        set_error("panda_server_submit: invalid argument");
+        return PANDA_ERR_INVALID_ARGUMENT;
+    }
+    if (k > kMaxK) {
+        set_error("panda_server_submit: k=%d above %d", k, kMaxK);
+        return PANDA_ERR_UNSUPPORTED;
+    }
+    if (m >= (1LL << 31)) {
+        set_error("panda_server_submit: m too large");
+        return PANDA_ERR_INVALID_ARGUMENT;
+    }
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (tree_id < 0 || tree_id >= (int32_t)S->trees.size()) {
+        set_error("panda_server_submit: unknown tree %d", tree_id);
+        return PANDA_ERR_INVALID_ARGUMENT;
+    }
+    if (S->stop) {
+        set_error("panda_server_submit: server is shutting down");
+        return PANDA_ERR_QUEUE_FULL;
+    }
+    Request R;
+    R.id = S->next_id++;
+    R.tree = tree_id;
+    R.queries = queries;
+    R.m = m;
+    R.k = k;
+    R.ids = out_ids;
+    R.d2 = out_d2;
+    R.t_submit = S->now_ns();
+    if (m == 0) {
+        R.done = true;
+        R.t_done = R.t_submit;
+    }
+    S->reqs[R.id] = R;
+    if (m > 0) S->pending.push_back(R.id);
+    *request_id = R.id;
+    S->cv.notify_all();
+    return PANDA_OK;
+}
+
+panda_status panda_server_poll(panda_server* S, int64_t request_id, int32_t* done)
+{
+    if (!S || !done) return PANDA_ERR_INVALID_ARGUMENT;
+    std::lock_guard<std::mutex> lk(S->mu);
+    auto it = S->reqs.find(request_id);
+    if (it == S->reqs.end()) {
+        set_error("panda_server_poll: unknown request %lld", (long long)request_id);
+        return PANDA_ERR_INVALID_ARGUMENT;
+    }
+    *done = it->second.done ? 1 : 0;
+    return it->second.done ? it->second.status : PANDA_OK;
+}
+
+panda_status panda_server_wait(panda_server* S, int64_t request_id, int64_t timeout_us)
+{
+    if (!S) return PANDA_ERR_INVALID_ARGUMENT;
+    std::unique_lock<std::mutex> lk(S->mu);
+    auto it = S->reqs.find(request_id);
+    if (it == S->reqs.end()) {
+        set_error("panda_server_wait: unknown request %lld", (long long)request_id);
+        return PANDA_ERR_INVALID_ARGUMENT;
+    }
+    const bool ok = S->cv.wait_for(lk, std::chrono::microseconds(std::max<int64_t>(timeout_us, 0)),
+                                   [&] { return S->reqs[request_id].done; });
+    if (!ok) {
+        set_error("panda_server_wait: request %lld not done after %lld us", (long long)request_id,
+                  (long long)timeout_us);
+        return PANDA_ERR_TIMEOUT;
+    }
+    return S->reqs[request_id].status;
+}
+
+panda_status panda_server_request_info(panda_server* S, int64_t request_id, int64_t* t_submit_ns,
+                                       int64_t* t_done_ns, int64_t* batch_id)
+{
+    if (!S) return PANDA_ERR_INVALID_ARGUMENT;
+    std::lock_guard<std::mutex> lk(S->mu);
+    auto it = S->reqs.find(request_id);
+    if (it == S->reqs.end()) return PANDA_ERR_INVALID_ARGUMENT;
+    if (t_submit_ns) *t_submit_ns = it->second.t_submit;
+    if (t_done_ns) *t_done_ns = it->second.t_done;
+    if (batch_id) *batch_id = it->second.batch;
+    return PANDA_OK;
+}
+
+int64_t panda_server_now_ns(panda_server* S) { return S ? S->now_ns() : -1; }
+
+panda_status panda_server_stats(panda_server* S, int64_t* batches, int64_t* requests, int64_t* pending,
+                                int64_t* bytes_used)
+{
+    if (!S) return PANDA_ERR_INVALID_ARGUMENT;
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (batches) *batches = S->batches;
+    if (requests) *requests = S->batched_requests;
+    if (pending) *pending = (int64_t)S->pending.size();
+    if (bytes_used) *bytes_used = S->used;
+    return PANDA_OK;
+}
+
+void panda_server_destroy(panda_server* S)
+{
+    if (!S) return;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->stop = true;
+    }
+    S->cv.notify_all();
+    if (S->sched.joinable()) S->sched.join();
+    cudaStreamSynchronize(S->qstream);
+    for (panda_tree* t : S->trees) panda_free(t);
+    cudaStreamDestroy(S->qstream);
+    cudaStreamDestroy(S->bstream);
+    delete S;
+}
+
+}  // extern "C"

@@ -39,6 +39,15 @@ SIGNATURES = {
     "panda_batch_status": ([_P, _P], ctypes.c_int),
     "panda_batch_info": ([_P, _P, _P], ctypes.c_int),
     "panda_batch_free": ([_P], None),
+    "panda_server_create": ([_I64, _I64, ctypes.POINTER(_P)], ctypes.c_int),
+    "panda_server_add_tree": ([_P, _P, _I64, _I32, _I32, _P], ctypes.c_int),
+    "panda_server_submit": ([_P, _I32, _P, _I64, _I32, _P, _P, _P], ctypes.c_int),
+    "panda_server_poll": ([_P, _I64, _P], ctypes.c_int),
+    "panda_server_wait": ([_P, _I64, _I64], ctypes.c_int),
+    "panda_server_request_info": ([_P, _I64, _P, _P, _P], ctypes.c_int),
+    "panda_server_now_ns": ([_P], _I64),
+    "panda_server_stats": ([_P, _P, _P, _P, _P], ctypes.c_int),
+    "panda_server_destroy": ([_P], None),
     "panda_free": ([_P], None),
     "panda_tree_get_info": ([_P, _P], ctypes.c_int),
     "panda_tree_copy": ([_P, _P, _P], ctypes.c_int),
@@ -274,6 +283,70 @@ class Batch:
     def __del__(self):
         try:
             self.free()
+        except Exception:
+            pass
+
+
+class Server:
+    """Served form: resident trees and continuous batching of KNN requests."""
+
+    def __init__(self, mem_budget_bytes: int = 0, max_batch_queries: int = 1 << 22):
+        h = ctypes.c_void_p()
+        _check(load().panda_server_create(int(mem_budget_bytes), int(max_batch_queries), ctypes.byref(h)))
+        self._h = h
+        self._keep = {}
+
+    def add_tree(self, points, bucket: int = 32) -> int:
+        p = _as_device_points(points, "points")
+        tid = ctypes.c_int32()
+        _check(load().panda_server_add_tree(self._h, ctypes.c_void_p(p.data_ptr()), p.shape[0], p.shape[1],
+                                            int(bucket), ctypes.byref(tid)))
+        return tid.value
+
+    def submit(self, tree_id: int, queries, k: int, out) -> int:
+        """Queue a request; `out` = (ids int32 [m][k], d2 float32 [m][k]) CUDA tensors."""
+        q = _as_device_points(queries, "queries")
+        ids, d2 = out
+        rid = ctypes.c_int64()
+        _check(load().panda_server_submit(self._h, int(tree_id), ctypes.c_void_p(q.data_ptr()), q.shape[0],
+                                          int(k), ctypes.c_void_p(ids.data_ptr()), ctypes.c_void_p(d2.data_ptr()),
+                                          ctypes.byref(rid)))
+        self._keep[rid.value] = (q, ids, d2)
+        return rid.value
+
+    def poll(self, rid: int) -> bool:
+        done = ctypes.c_int32()
+        _check(load().panda_server_poll(self._h, int(rid), ctypes.byref(done)))
+        return bool(done.value)
+
+    def wait(self, rid: int, timeout_s: float = 60.0):
+        _check(load().panda_server_wait(self._h, int(rid), int(timeout_s * 1e6)))
+        self._keep.pop(rid, None)
+
+    def times(self, rid: int):
+        """(submit ns, done ns, batch id) on the server's clock."""
+        a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        _check(load().panda_server_request_info(self._h, int(rid), ctypes.byref(a), ctypes.byref(b),
+                                                ctypes.byref(c)))
+        return a.value, b.value, c.value
+
+    def now_ns(self) -> int:
+        return int(load().panda_server_now_ns(self._h))
+
+    def stats(self) -> dict:
+        v = [ctypes.c_int64() for _ in range(4)]
+        _check(load().panda_server_stats(self._h, *[ctypes.byref(x) for x in v]))
+        return dict(zip(["batches", "requests", "pending", "bytes_used"], [x.value for x in v]))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().panda_server_destroy(self._h)
+            self._h = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
         except Exception:
             pass
 

@@ -1,0 +1,125 @@
+"""Served form: requests of different trees, sizes and k coalesced into shared
+launches return exactly what each request returns alone (panda_knn on the
+same tree), a tree can be admitted while requests run, and admission respects
+the memory budget."""
+import threading
+
+import numpy as np
+import pytest
+
+from paper_1607_08220_gb300 import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_1607_08220_gb300 import build_ext, panda
+    build_ext.build()
+    panda.load()
+    return panda
+
+
+def alone(P, tree, q, k):
+    import torch
+    ids, d2 = P.knn(tree, q, k)
+    torch.cuda.synchronize()
+    return ids, d2
+
+
+def test_mixed_requests_equal_alone(P):
+    import torch
+    rng = np.random.default_rng(5)
+    pts_a = torch.from_numpy(workloads.cosmology_points(200_000, seed=50, halos=30)).cuda()
+    pts_b = torch.from_numpy(workloads.plasma_points(150_000, seed=51)).cuda()
+    srv = P.Server(max_batch_queries=40_000)
+    ta, tb = srv.add_tree(pts_a), srv.add_tree(pts_b)
+    ref_a, ref_b = P.build(pts_a, 32), P.build(pts_b, 32)
+    todo = []
+    for i in range(80):
+        tree = int(rng.integers(0, 2))
+        m = int(np.floor(np.exp(rng.uniform(0, np.log(20_001)))))
+        k = int(rng.choice([1, 8, 32]))
+        q = (workloads.cosmology_points(m, seed=1000 + i, halos=30) if tree == 0
+             else workloads.plasma_points(m, seed=1000 + i))
+        qd = torch.from_numpy(q).cuda()
+        out = (torch.empty((m, k), dtype=torch.int32, device="cuda"),
+               torch.empty((m, k), dtype=torch.float32, device="cuda"))
+        todo.append((tree, qd, k, out))
+    torch.cuda.synchronize()
+    reqs = [(srv.submit([ta, tb][tree], qd, k, out), tree, qd, k, out) for tree, qd, k, out in todo]
+    for rid, tree, qd, k, out in reqs:
+        srv.wait(rid, 60)
+        ri, rd = alone(P, [ref_a, ref_b][tree], qd, k)
+        assert torch.equal(out[0], ri)
+        assert torch.equal(out[1].view(torch.int32), rd.view(torch.int32))
+    st = srv.stats()
+    assert st["requests"] == 80 and st["batches"] < 80          # requests were coalesced
+    batches = {srv.times(r[0])[2] for r in reqs}
+    assert len(batches) == st["batches"]
+    srv.close()
+
+
+def test_tree_admitted_while_requests_run(P):
+    import torch
+    pts_a = torch.from_numpy(workloads.cosmology_points(300_000, seed=60, halos=40)).cuda()
+    pts_b = torch.from_numpy(workloads.cosmology_points(250_000, seed=61, halos=40)).cuda()
+    srv = P.Server(max_batch_queries=1 << 20)
+    ta = srv.add_tree(pts_a)
+    ref_a, ref_b = P.build(pts_a, 32), P.build(pts_b, 32)
+    result = {}
+
+    def admit():
+        result["tb"] = srv.add_tree(pts_b)
+
+    th = threading.Thread(target=admit)
+    reqs = []
+    for i in range(30):
+        if i == 5:
+            th.start()
+        qd = torch.from_numpy(workloads.cosmology_points(20_000, seed=2000 + i, halos=40)).cuda()
+        out = (torch.empty((20_000, 8), dtype=torch.int32, device="cuda"),
+               torch.empty((20_000, 8), dtype=torch.float32, device="cuda"))
+        reqs.append((srv.submit(ta, qd, 8, out), ref_a, qd, out))
+    th.join()
+    qd = torch.from_numpy(workloads.cosmology_points(10_000, seed=3000, halos=40)).cuda()
+    out = (torch.empty((10_000, 5), dtype=torch.int32, device="cuda"),
+           torch.empty((10_000, 5), dtype=torch.float32, device="cuda"))
+    reqs.append((srv.submit(result["tb"], qd, 5, out), ref_b, qd, out))
+    for rid, ref, qd, out in reqs:
+        srv.wait(rid, 60)
+        ri, rd = alone(P, ref, qd, out[0].shape[1])
+        assert torch.equal(out[0], ri) and torch.equal(out[1].view(torch.int32), rd.view(torch.int32))
+    srv.close()
+
+
+def test_admission_budget_and_errors(P):
+    import torch
+    pts = torch.from_numpy(np.random.default_rng(0).random((100_000, 3), dtype=np.float32)).cuda()
+    srv = P.Server(mem_budget_bytes=1 << 20)       # 1 MiB: a 100k-point tree does not fit
+    with pytest.raises(P.PandaError) as e:
+        srv.add_tree(pts)
+    assert e.value.status == 4
+    srv.close()
+    srv = P.Server()
+    t = srv.add_tree(pts)
+    q = pts[:100]
+    out = (torch.empty((100, 65), dtype=torch.int32, device="cuda"),
+           torch.empty((100, 65), dtype=torch.float32, device="cuda"))
+    with pytest.raises(P.PandaError) as e:
+        srv.submit(t, q, 65, out)
+    assert e.value.status == 3
+    with pytest.raises(P.PandaError) as e:
+        srv.submit(t + 7, q, 4, out)
+    assert e.value.status == 1
+    with pytest.raises(P.PandaError) as e:
+        srv.wait(123456, 0.01)
+    assert e.value.status == 1
+    out = (torch.empty((100, 4), dtype=torch.int32, device="cuda"),
+           torch.empty((100, 4), dtype=torch.float32, device="cuda"))
+    rid = srv.submit(t, q, 4, out)
+    srv.wait(rid, 30)
+    assert torch.equal(out[0][:, 0].cpu(), torch.arange(100, dtype=torch.int32))
+    srv.close()
