@@ -41,8 +41,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["cosmology_self", "uniform_small", "features_10d", "batched_sets"],
+    ap.add_argument("--workload", choices=["cosmology_self", "uniform_small", "features_10d", "batched_sets",
+                                           "plasma_serving", "features_10d_served"],
                     default="cosmology_self")
+    ap.add_argument("--duration", type=float, default=1.0, help="seconds of the served request stream")
     ap.add_argument("--nsets", type=int, default=512, help="sets of the batched workload")
     ap.add_argument("--order", choices=["leaf", "morton", "none"], default="leaf")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -428,7 +430,12 @@ def run_batched(args):
     nq = [q.shape[0] for _, q, _ in sets]
     ks = [k for _, _, k in sets]
     m_total = sum(nq)
-    batch = P.Batch(npts, nq, ks, d=3, bucket=32)
+    # the autotuner picks the bucket size and the scan shape on the largest set
+    big = int(np.argmax(npts))
+    tuned = P.tune(torch.from_numpy(sets[big][0]).cuda(), torch.from_numpy(sets[big][1]).cuda(),
+                   k=ks[big], m_total=nq[big])
+    batch = P.Batch(npts, nq, ks, d=3, bucket=tuned["bucket"])
+    batch.set_query_params(tuned["transpose_max"], tuned["traversal"])
     for s_, (pts, q, k) in enumerate(sets):
         batch.points[batch.point_off[s_]:batch.point_off[s_ + 1]].copy_(torch.from_numpy(pts))
         batch.queries[batch.query_off[s_]:batch.query_off[s_ + 1]].copy_(torch.from_numpy(q))
@@ -457,7 +464,7 @@ def run_batched(args):
 
     def plain_step():
         for i in range(len(sets)):
-            t = P.build(pts_d[i], 32)
+            t = P.build(pts_d[i], tuned["bucket"])
             if nq[i]:
                 P.knn(t, q_d[i], ks[i], out=outs[i])
             t.free()
@@ -481,17 +488,162 @@ def run_batched(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
             "config": {"workload": f"batched_sets: {len(sets)} sets, sizes log-uniform [1e3, 2e6], "
-                                   f"{sum(npts)} points, {m_total} queries, k in {{4,8,16,32}}, B=32",
+                                   f"{sum(npts)} points, {m_total} queries, k in {{4,8,16,32}}, "
+                                   f"B={tuned['bucket']} (autotuned)",
                        "sets": len(sets), "points": int(sum(npts)), "queries": int(m_total),
                        "step": "build every set's tree + answer every set's queries (one graph launch)",
                        "l2": "inputs larger than L2"},
             "clocks": clk, "gpu_launches": int(info["kernels_per_run"]) * args.steps,
             "plain": {"value": m_total / (p_ms / 1e3), "ms_per_step": p_ms,
                       "path": "one panda_build + one panda_knn per set, serialised on one stream"},
-            "speedup_vs_plain": p_ms / b_ms, "identical_to_plain": bool(same),
+            "speedup_vs_plain": p_ms / b_ms, "identical_to_plain": bool(same), "autotuned": tuned,
             "build_pts_per_s": sum(npts) / (b_ms / 1e3), "generation_s": gen_s}
     print(json.dumps(line), flush=True)
     batch.free()
+    return 0
+
+
+def _latency_stats(lat_ms):
+    a = np.sort(np.asarray(lat_ms))
+    return {"p50_ms": float(np.percentile(a, 50)), "p99_ms": float(np.percentile(a, 99)),
+            "mean_ms": float(a.mean()), "max_ms": float(a.max())}
+
+
+def run_served(args):
+    """Served form on a Poisson request stream vs the plain path (one panda_knn
+    per request, in arrival order, one at a time)."""
+    import threading
+
+    import torch
+
+    import paper_1607_08220_gb300 as P
+    from paper_1607_08220_gb300 import build_ext, workloads
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    build_ext.build()
+    P.load()
+    t_gen = time.time()
+    if args.workload == "plasma_serving":
+        trees_np = [workloads.plasma_points(100_000_000, seed=0)]
+        second = workloads.plasma_points(20_000_000, seed=4)
+        reqs = workloads.plasma_requests(duration_s=args.duration)
+        def qgen(r):
+            return workloads.plasma_points(r["m"], seed=r["seed"])
+        desc = (f"plasma_serving: resident tree of 1e8 slab points, Poisson {len(reqs)} requests over "
+                f"{args.duration:g} s (2,000/s), sizes log-uniform [1, 1e6], k in {{1, 8, 32}}, second tree "
+                f"of 2e7 points admitted at 0.5 s")
+    else:
+        w = workloads.features_10d()
+        trees_np = [w.points]
+        second = None
+        sizes = w.meta["request_sizes"]
+        rng = np.random.default_rng(6)
+        arrivals = np.sort(rng.uniform(0.0, args.duration, len(sizes)))
+        offs = np.concatenate([[0], np.cumsum(sizes)])
+        reqs = [dict(t=float(arrivals[i]), m=int(sizes[i]), k=w.k, tree=0, row=int(offs[i]))
+                for i in range(len(sizes))]
+        def qgen(r):
+            return w.queries[r["row"]:r["row"] + r["m"]]
+        desc = (f"features_10d served: tree of 2^23 10-D points, 2^20 held-out queries in {len(reqs)} "
+                f"requests of log-uniform size arriving uniformly over {args.duration:g} s, k=16")
+    d = trees_np[0].shape[1]
+    qdev = [torch.from_numpy(np.ascontiguousarray(qgen(r))).cuda() for r in reqs]
+    outs = [(torch.empty((r["m"], r["k"]), dtype=torch.int32, device="cuda"),
+             torch.empty((r["m"], r["k"]), dtype=torch.float32, device="cuda")) for r in reqs]
+    pts_dev = [torch.from_numpy(trees_np[0]).cuda()]
+    sec_dev = torch.from_numpy(second).cuda() if second is not None else None
+    gen_s = time.time() - t_gen
+    m_total = sum(r["m"] for r in reqs)
+    torch.cuda.synchronize()
+
+    # ---- served
+    srv = P.Server(max_batch_queries=1 << 22)
+    tb0 = time.time()
+    tree_ids = [srv.add_tree(pts_dev[0])]
+    build_first_s = time.time() - tb0
+    admitted = threading.Event()
+    admit_info = {}
+
+    def admit():
+        t = time.time()
+        tree_ids.append(srv.add_tree(sec_dev))
+        admit_info["build_s"] = time.time() - t
+        admitted.set()
+
+    clocks = ClockSampler(os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0].strip())
+    clocks.start()
+    t0 = srv.now_ns() + 20_000_000            # stream starts 20 ms from now
+    rids = [None] * len(reqs)
+    admitter = None
+    for i, r in enumerate(reqs):
+        due = t0 + int(r["t"] * 1e9)
+        if sec_dev is not None and admitter is None and r["t"] >= 0.5:
+            admitter = threading.Thread(target=admit)
+            admitter.start()
+        while srv.now_ns() < due:
+            pass
+        if r["tree"] == 1:
+            admitted.wait()
+        rids[i] = srv.submit(tree_ids[r["tree"]], qdev[i], r["k"], outs[i])
+    for rid in rids:
+        srv.wait(rid, 600)
+    if admitter is not None:
+        admitter.join()
+    clk = clocks.stop()
+    done = [srv.times(rid)[1] for rid in rids]
+    lat = [(done[i] - (t0 + int(r["t"] * 1e9))) / 1e6 for i, r in enumerate(reqs)]
+    span_s = (max(done) - t0) / 1e9
+    st = srv.stats()
+    served = {"value": m_total / span_s, "unit": UNIT, **_latency_stats(lat), "batches": st["batches"],
+              "requests_per_batch": st["requests"] / max(st["batches"], 1), "span_s": span_s}
+    # capacity: every request submitted at once
+    tb = srv.now_ns()
+    brids = [srv.submit(tree_ids[r["tree"]], qdev[i], r["k"], outs[i]) for i, r in enumerate(reqs)]
+    for rid in brids:
+        srv.wait(rid, 600)
+    bspan = (max(srv.times(rid)[1] for rid in brids) - tb) / 1e9
+    st2 = srv.stats()
+    served["burst_value"] = m_total / bspan
+    served["burst_s"] = bspan
+    served["burst_batches"] = st2["batches"] - st["batches"]
+
+    # ---- plain path: the same stream, one synchronous panda_knn per request, FIFO
+    plain_trees = [P.build(pts_dev[0], 32)] + ([P.build(sec_dev, 32)] if sec_dev is not None else [])
+    ref = [(torch.empty_like(o[0]), torch.empty_like(o[1])) for o in outs]
+    torch.cuda.synchronize()
+    base = time.perf_counter() + 0.02
+    plat, fin = [], 0.0
+    for i, r in enumerate(reqs):
+        due = base + r["t"]
+        while time.perf_counter() < due:
+            pass
+        P.knn(plain_trees[r["tree"]], qdev[i], r["k"], out=ref[i])
+        torch.cuda.current_stream().synchronize()
+        fin = time.perf_counter()
+        plat.append((fin - due) * 1e3)
+    pspan = fin - base
+    plain = {"value": m_total / pspan, "unit": UNIT, **_latency_stats(plat), "span_s": pspan,
+             "path": "one panda_knn per request in arrival order, synchronised after each"}
+    tp = time.perf_counter()
+    for i, r in enumerate(reqs):
+        P.knn(plain_trees[r["tree"]], qdev[i], r["k"], out=ref[i])
+        torch.cuda.current_stream().synchronize()
+    plain["burst_s"] = time.perf_counter() - tp
+    plain["burst_value"] = m_total / plain["burst_s"]
+    same = all(torch.equal(outs[i][0], ref[i][0]) and torch.equal(outs[i][1].view(torch.int32),
+                                                                   ref[i][1].view(torch.int32))
+               for i in range(len(reqs)))
+    srv.close()
+    line = {"metric": METRIC + " [served form]", "value": served["value"], "unit": UNIT, "n_gpus": 1,
+            "steps": 1, "warmup": 0, "ms_per_step": span_s * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": desc, "requests": len(reqs), "queries": int(m_total),
+                       "l2": "inputs larger than L2"},
+            "clocks": clk, "served": served, "plain": plain,
+            "speedup_vs_plain": served["burst_value"] / plain["burst_value"],
+            "speedup_note": "capacity (all requests submitted at once), served vs plain",
+            "identical_to_plain": bool(same), "first_tree_build_s": build_first_s,
+            "second_tree_admit_build_s": admit_info.get("build_s"), "generation_s": gen_s}
+    print(json.dumps(line), flush=True)
     return 0
 
 
@@ -501,6 +653,8 @@ def main():
         return run_reference(args)
     if args.workload == "batched_sets":
         return run_batched(args)
+    if args.workload in ("plasma_serving", "features_10d_served"):
+        return run_served(args)
     return run_ours(args)
 
 

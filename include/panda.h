@@ -77,7 +77,17 @@ typedef struct panda_query_params {
                                (queries broadcast in turn), otherwise with lanes holding
                                queries; 0 = default (12), 32 = always the former,
                                -1 = always the latter.  Never changes results. */
+    int32_t traversal;      /* PANDA_TRAVERSAL_*: 0 = automatic (per-query when the
+                               queries are sparse: fewer than n/4), never changes results */
+    int32_t reserved;
 } panda_query_params;
+
+/* Traversal shape of the KNN kernel. */
+enum {
+    PANDA_TRAVERSAL_AUTO = 0,
+    PANDA_TRAVERSAL_PACKET = 1,   /* a warp's 32 spatially grouped queries share one stack */
+    PANDA_TRAVERSAL_PER_QUERY = 2 /* each lane walks its own query with its own stack */
+};
 
 typedef struct panda_tree_info {
     int64_t n;          /* points */
@@ -167,6 +177,12 @@ panda_status panda_batch_buffers(panda_batch* batch, float** points, float** que
 /* point_off, query_off, out_off: host arrays of nsets + 1 entries (each may be NULL). */
 panda_status panda_batch_offsets(const panda_batch* batch, int64_t* point_off, int64_t* query_off,
                                  int64_t* out_off);
+/* Query parameters of the batch's traversal (order must be PANDA_ORDER_LEAF
+ * or params NULL for defaults).  traversal AUTO chooses per set (per-query
+ * when the set has fewer than n/4 queries); PACKET or PER_QUERY applies to
+ * every set.  After a run this waits for the whole device and drops the
+ * captured graph; the next panda_batch_run captures it again. */
+panda_status panda_batch_set_query_params(panda_batch* batch, const panda_query_params* params);
 panda_status panda_batch_run(panda_batch* batch, void* stream);
 panda_status panda_batch_status(panda_batch* batch, void* stream);
 /* Forest statistics of the last run; *kernels_per_run = kernels in the captured graph. */
@@ -202,6 +218,29 @@ panda_status panda_server_stats(panda_server* server, int64_t* batches, int64_t*
                                 int64_t* bytes_used);
 /* Finishes queued and running requests, then releases every tree and the server. */
 void panda_server_destroy(panda_server* server);
+
+/* ---- autotuner ------------------------------------------------------------------
+ * Times every combination of bucket size {16, 32, 64}, query order {none,
+ * Morton, leaf}, traversal shape {packet with scan-shape switch -1, 4, 8, 12,
+ * 16, 32 (see panda_query_params.transpose_max), per-query} on the given
+ * device points and a device
+ * sample of queries ([m_sample][d]), and returns the combination with the
+ * smallest build time + query time scaled to m_total queries per build.  None
+ * of these knobs changes a result.  The choice is also cached per (d,
+ * ceil(log2 n), k, ceil(log2 m_total)) for panda_tune_lookup.  Builds 6 trees. */
+typedef struct panda_tune_result {
+    int32_t bucket;
+    int32_t order;          /* panda_order */
+    int32_t transpose_max;  /* for panda_query_params */
+    int32_t traversal;      /* PANDA_TRAVERSAL_PACKET or _PER_QUERY */
+    float build_ms;         /* timed build with this bucket */
+    float query_ms;         /* query time scaled to m_total queries */
+    float score_ms;         /* build_ms + query_ms */
+    float reserved2;
+} panda_tune_result;
+panda_status panda_tune(const float* points, int64_t n, int32_t d, const float* queries, int64_t m_sample,
+                        int64_t m_total, int32_t k, void* stream, panda_tune_result* out);
+panda_status panda_tune_lookup(int32_t d, int64_t n, int32_t k, int64_t m_total, panda_tune_result* out);
 
 /* ---- inspection -------------------------------------------------------------
  * panda_tree_get_info fills *info.  panda_tree_copy copies the tree's node

@@ -6,7 +6,7 @@ The compute path is the CUDA library ``_lib/libpanda.so`` behind the C ABI in
 with :func:`paper_1607_08220_gb300.build_ext.build`.
 """
 from .panda import (Batch, PandaError, Server, Tree, build, build_host, kernel_launches, knn, knn_host, knn_sync, knn_visits,
-                    load, phase_times, set_phase_timing, version)
+                    load, phase_times, set_phase_timing, tune, tune_lookup, version)
 
 __all__ = ["Batch", "PandaError", "Server", "Tree", "build", "build_host", "knn", "knn_host", "knn_sync", "knn_visits", "load",
-           "phase_times", "set_phase_timing", "kernel_launches", "version"]
+           "phase_times", "set_phase_timing", "kernel_launches", "tune", "tune_lookup", "version"]

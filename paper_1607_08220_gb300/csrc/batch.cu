@@ -48,6 +48,8 @@ struct panda_batch {
     unsigned* d_err = nullptr;
     cudaGraphExec_t exec = nullptr;
     int64_t kernels_per_run = 0;
+    int transpose_max = 12;
+    int traversal = PANDA_TRAVERSAL_AUTO;
     std::vector<void*> owned;
 };
 
@@ -123,7 +125,7 @@ panda_status batch_enqueue(panda_batch* b, cudaStream_t s)
     ka.m = b->m_total;
     ka.d = b->d;
     ka.k = b->kmax;
-    ka.transpose_max = 12;
+    ka.transpose_max = b->transpose_max;
     return launch_multi(ka, padded_dim(b->d), s);
 }
 
@@ -244,6 +246,7 @@ panda_status panda_batch_create(const panda_set_desc* sets, int32_t nsets, int32
         S.id_base = (int)b->poff[s];
         S.k = b->ks[s];
         S.row_base = (int)b->qoff[s];
+        S.solo = 4 * b->nq[s] < b->np[s];
         for (long long p = 0; p < b->nq[s]; p += 32) hj.push_back(KnnJob{s, (int)p});
     }
     b->njobs = (int)hj.size();
@@ -294,6 +297,34 @@ panda_status panda_batch_offsets(const panda_batch* b, int64_t* point_off, int64
         if (point_off) point_off[s] = b->poff[s];
         if (query_off) query_off[s] = b->qoff[s];
         if (out_off) out_off[s] = b->ooff[s];
+    }
+    return PANDA_OK;
+}
+
+panda_status panda_batch_set_query_params(panda_batch* b, const panda_query_params* params)
+{
+    if (!b) return PANDA_ERR_INVALID_ARGUMENT;
+    if (params && params->order != PANDA_ORDER_LEAF) {
+        set_error("panda_batch_set_query_params: a batch orders queries by leaf");
+        return PANDA_ERR_UNSUPPORTED;
+    }
+    if (b->exec) {
+        // the parameters are baked into the captured graph: wait for every run
+        // in flight, drop the graph, and capture again at the next run
+        PANDA_CUDA(cudaDeviceSynchronize(), "panda_batch_set_query_params: wait for runs in flight");
+        cudaGraphExecDestroy(b->exec);
+        b->exec = nullptr;
+    }
+    b->transpose_max = (params && params->transpose_max != 0) ? params->transpose_max : 12;
+    b->traversal = params ? params->traversal : PANDA_TRAVERSAL_AUTO;
+    if (b->traversal != PANDA_TRAVERSAL_AUTO) {
+        // rewrite the set descriptors with the requested traversal shape
+        std::vector<KnnSet> hs(b->nsets);
+        PANDA_CUDA(cudaMemcpy(hs.data(), b->d_sets, b->nsets * sizeof(KnnSet), cudaMemcpyDeviceToHost),
+                   "panda_batch_set_query_params");
+        for (KnnSet& S : hs) S.solo = b->traversal == PANDA_TRAVERSAL_PER_QUERY;
+        PANDA_CUDA(cudaMemcpy(b->d_sets, hs.data(), b->nsets * sizeof(KnnSet), cudaMemcpyHostToDevice),
+                   "panda_batch_set_query_params");
     }
     return PANDA_OK;
 }

@@ -13,7 +13,10 @@ panda_status configure_knn()
 {
     static bool configured = false;
     if (!configured) {
-        PANDA_CUDA(cudaFuncSetAttribute(k_knn<DP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        PANDA_CUDA(cudaFuncSetAttribute(k_knn<DP, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        kMaxK * kKnnThreads * 8),
+                   "configure k_knn");
+        PANDA_CUDA(cudaFuncSetAttribute(k_knn<DP, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         kMaxK * kKnnThreads * 8),
                    "configure k_knn");
         configured = true;
@@ -33,7 +36,10 @@ panda_status launch_knn_dp(const KnnArgs& a, cudaStream_t s)
                                     : (warps + kKnnThreads / 32 - 1) / (kKnnThreads / 32);
     if (blocks <= 0) return PANDA_OK;
     const size_t heap_bytes = (size_t)a.k * kKnnThreads * 8;
-    k_knn<DP><<<(unsigned)blocks, kKnnThreads, heap_bytes, s>>>(a);
+    if (a.jobs || a.solo)
+        k_knn<DP, true><<<(unsigned)blocks, kKnnThreads, heap_bytes, s>>>(a);
+    else
+        k_knn<DP, false><<<(unsigned)blocks, kKnnThreads, heap_bytes, s>>>(a);
     PANDA_LAUNCHED("k_knn");
     return PANDA_OK;
 }

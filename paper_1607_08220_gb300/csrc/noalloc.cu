@@ -135,8 +135,9 @@ extern "C" panda_status panda_knn_noalloc(const panda_tree* t, const float* quer
         oa.d = t->d;
         oa.ns = t->ns;
         oa.mode = PANDA_ORDER_LEAF;
+        const long long want = std::max<long long>(4096, std::min<long long>(kNoAllocBins - 1, 4 * m));
         int sh = 0;
-        while (((long long)t->n >> sh) + 1 > kNoAllocBins) sh++;
+        while (((long long)t->n >> sh) > want) sh++;
         oa.shift = sh;
         const int nb = (int)(((long long)t->n >> sh) + 1);
         const int nblk = (nb + 4095) / 4096;
@@ -170,5 +171,6 @@ extern "C" panda_status panda_knn_noalloc(const panda_tree* t, const float* quer
     ka.d = t->d;
     ka.k = k;
     ka.transpose_max = 12;
+    ka.solo = 4 * m < t->n;
     return launch_traversal(ka, t->dp, s);
 }

@@ -225,8 +225,11 @@ panda_status knn_query(const panda_tree* t, const float* queries, int64_t m, int
                 oa.inv[j] = w > 0.0f ? 1.0f / w : 0.0f;
             }
         } else {
+            // about four bins per query (at least 4096, at most 2^22): the
+            // histogram scan then costs no more than the queries themselves
+            const long long want = std::max<long long>(4096, std::min<long long>(1LL << 22, 4 * m));
             int sh = 0;
-            while (((long long)t->n >> sh) > (1 << 22)) sh++;
+            while (((long long)t->n >> sh) > want) sh++;
             oa.shift = sh;
             nb = (int)(((long long)t->n >> sh) + 1);
         }
@@ -267,6 +270,10 @@ panda_status knn_query(const panda_tree* t, const float* queries, int64_t m, int
     ka.visits = visits;
     ka.stats = stats;
     ka.transpose_max = (params && params->transpose_max != 0) ? params->transpose_max : 12;
+    {
+        const int tr = params ? params->traversal : PANDA_TRAVERSAL_AUTO;
+        ka.solo = tr == PANDA_TRAVERSAL_PER_QUERY ? 1 : tr == PANDA_TRAVERSAL_PACKET ? 0 : (4 * m < t->n);
+    }
     ka.d = t->d;
     ka.k = k;
     st = launch_knn(ka, t->dp, stream);

@@ -43,6 +43,8 @@ struct KnnSet {
     float* d2;
     long long m;
     int root, id_base, k, row_base;
+    int solo;   // 1: each lane walks its own query (sparse query sets); 0: warp packets
+    int pad;
 };
 // A warp job: traversal positions [pos, pos + 32) of one set.
 struct KnnJob {
@@ -68,6 +70,7 @@ struct KnnArgs {
     long long npts;
     int d, k;
     int transpose_max;    // use the transposed scan when at most this many lanes need a bucket
+    int solo;             // single-tree launch: traversal shape (see KnnSet::solo)
 };
 
 constexpr unsigned long long kKeyEmpty = (0x7f800000ull << 32) | 0xffffffffull;
@@ -92,8 +95,124 @@ __device__ __forceinline__ void heap_replace_root(unsigned long long* h, int k, 
     h[i * kKnnThreads] = c;
 }
 
-// Traversal of one warp job: positions [g0, g0 + 32) of set S.
+// Squared distance from q to the tight box of a node record (dims in order, unfused).
 template <int DP>
+__device__ __forceinline__ float record_box_d2(const float4* rec, const float (&q)[DP])
+{
+    constexpr int NS = (4 + 2 * DP + 3) / 4;
+    float f[4 * NS];
+#pragma unroll
+    for (int r = 1; r < NS; r++) {
+        const float4 v = __ldg(rec + r);
+        f[4 * r] = v.x;
+        f[4 * r + 1] = v.y;
+        f[4 * r + 2] = v.z;
+        f[4 * r + 3] = v.w;
+    }
+    float bnd = 0.0f;
+#pragma unroll
+    for (int k = 0; k < DP; k++) {
+        const float g = fmaxf(fmaxf(__fsub_rn(f[4 + k], q[k]), __fsub_rn(q[k], f[4 + DP + k])), 0.0f);
+        bnd = __fadd_rn(bnd, __fmul_rn(g, g));
+    }
+    return bnd;
+}
+
+// One lane walks its own query (Algorithm 1 as written, with the corrections):
+// its own stack of (node, bound) where a child's bound is its box distance,
+// computed at the parent; the far child is pushed only if its bound does not
+// exceed r', the near child last; buckets are scanned point by point.
+template <int DP>
+__device__ __forceinline__ void knn_lane_solo(const KnnArgs& a, const KnnSet& S, const float (&q)[DP],
+                                              unsigned long long* h, int K, unsigned long long& kth,
+                                              int& vnodes, int& vpts)
+{
+    constexpr int NV = (DP + 1 + 3) / 4;
+    constexpr int NS = (4 + 2 * DP + 3) / 4;
+    int stn[kMaxDepth + 4];
+    float stb[kMaxDepth + 4];
+    int sp = 0;
+    stn[sp] = S.root;
+    stb[sp] = 0.0f;
+    sp++;
+    long long budget = 2LL * S.num_nodes + 8;
+    while (sp > 0) {
+        if (--budget < 0) {
+            atomicOr(a.err, kErrInternal);
+            break;
+        }
+        sp--;
+        const int node = stn[sp];
+        const float kd = __uint_as_float((unsigned)(kth >> 32));
+        if (stb[sp] > kd) continue;
+        if ((unsigned)node >= (unsigned)S.num_nodes) {
+            atomicOr(a.err, kErrInternal);
+            break;
+        }
+        const float4* rec = S.nodes + (long long)node * NS;
+        const int4 hd = __ldg(reinterpret_cast<const int4*>(rec));
+        vnodes++;
+        if ((unsigned)hd.w & kMetaLeaf) {
+            if (hd.x < 0 || hd.y < 0 || (long long)hd.x + hd.y > S.npts) {
+                atomicOr(a.err, kErrInternal);
+                break;
+            }
+            vpts += hd.y;
+            for (int j = 0; j < hd.y; j++) {
+                const float4* src = S.pts + (long long)(hd.x + j) * NV;
+                float pv[4 * NV];
+#pragma unroll
+                for (int v = 0; v < NV; v++) {
+                    const float4 p = __ldg(src + v);
+                    pv[4 * v] = p.x;
+                    pv[4 * v + 1] = p.y;
+                    pv[4 * v + 2] = p.z;
+                    pv[4 * v + 3] = p.w;
+                }
+                float acc = 0.0f;
+#pragma unroll
+                for (int k = 0; k < DP; k++) {
+                    const float t = __fsub_rn(q[k], pv[k]);
+                    acc = k == 0 ? __fmul_rn(t, t) : __fadd_rn(acc, __fmul_rn(t, t));
+                }
+                const unsigned long long key =
+                    ((unsigned long long)__float_as_uint(acc) << 32) | (unsigned)__float_as_int(pv[DP]);
+                if (key < kth) {
+                    heap_replace_root(h, K, key);
+                    kth = h[0];
+                }
+            }
+        } else {
+            const int c0 = hd.x;
+            if ((unsigned)(c0 + 1) >= (unsigned)S.num_nodes || sp + 2 > kMaxDepth + 4) {
+                atomicOr(a.err, kErrInternal);
+                break;
+            }
+            const float b0 = record_box_d2<DP>(S.nodes + (long long)c0 * NS, q);
+            const float b1 = record_box_d2<DP>(S.nodes + (long long)(c0 + 1) * NS, q);
+            const int dim = (int)((unsigned)hd.w & kMetaDimMask);
+            float qd = 0.0f;
+#pragma unroll
+            for (int k = 0; k < DP; k++)
+                if (k == dim) qd = q[k];
+            const bool right_near = qd >= __int_as_float(hd.z);
+            const float bn = right_near ? b1 : b0, bf = right_near ? b0 : b1;
+            if (bf <= kd) {
+                stn[sp] = right_near ? c0 : c0 + 1;   // far child first
+                stb[sp] = bf;
+                sp++;
+            }
+            stn[sp] = right_near ? c0 + 1 : c0;       // near child last
+            stb[sp] = bn;
+            sp++;
+        }
+    }
+}
+
+// Traversal of one warp job: positions [g0, g0 + 32) of set S.  SOLO_OK
+// compiles the per-query traversal in (taken when S.solo is set); without it
+// the kernel holds the packet traversal alone and keeps its registers.
+template <int DP, bool SOLO_OK>
 __device__ __forceinline__ void knn_warp_job(const KnnArgs& a, const KnnSet& S, long long g0,
                                              float (*sx)[32], int* sid, unsigned long long* h)
 {
@@ -117,17 +236,20 @@ __device__ __forceinline__ void knn_warp_job(const KnnArgs& a, const KnnSet& S, 
     // k-th best key so far (the heap root); invalid lanes never accept anything
     unsigned long long kth = valid ? kKeyEmpty : 0ull;
 
+    int vnodes = 0, vpts = 0;
+    // diagnostics: inner nodes, leaf chunks, lanes=queries chunks, transposed
+    // broadcasts, insertion-loop rounds, candidates, insertions
+    unsigned st[7] = {0, 0, 0, 0, 0, 0, 0};
+    const bool stats = a.stats != nullptr;
+    if (SOLO_OK && S.solo) {
+        if (valid) knn_lane_solo<DP>(a, S, q, h, K, kth, vnodes, vpts);
+    } else {
     int stack[kMaxDepth + 4];
     int sp = 0;
     stack[sp++] = S.root;
     // A valid tree is visited in at most 2 * num_nodes pops; the cap only
     // guarantees termination (with an error flag) should a node table be corrupt.
     long long budget = 2LL * S.num_nodes + 8;
-    int vnodes = 0, vpts = 0;
-    // diagnostics: inner nodes, leaf chunks, lanes=queries chunks, transposed
-    // broadcasts, insertion-loop rounds, candidates, insertions
-    unsigned st[7] = {0, 0, 0, 0, 0, 0, 0};
-    const bool stats = a.stats != nullptr;
     while (sp > 0) {
         if (--budget < 0 || (unsigned)stack[sp - 1] >= (unsigned)S.num_nodes) {
             if (lane == 0) atomicOr(a.err, kErrInternal);
@@ -273,6 +395,8 @@ __device__ __forceinline__ void knn_warp_job(const KnnArgs& a, const KnnSet& S, 
             stack[sp++] = h0 + (right_near ? 1 : 0);   // near child last
         }
     }
+    }   // packet traversal
+    __syncwarp();
     if (stats) {
         // st[0..4] are warp-uniform (counted once per warp); 5, 6 are per lane
         st[5] = __reduce_add_sync(kFull, st[5]);
@@ -301,7 +425,9 @@ __device__ __forceinline__ void knn_warp_job(const KnnArgs& a, const KnnSet& S, 
 }
 
 
-template <int DP>
+// GENERAL = false: one tree, packet traversal only.  GENERAL = true: one tree
+// or many sets, each set's traversal shape chosen by its solo flag.
+template <int DP, bool GENERAL>
 __global__ void __launch_bounds__(kKnnThreads) k_knn(KnnArgs a)
 {
     __shared__ __align__(16) float stage_x[kKnnThreads / 32][DP][32];
@@ -309,7 +435,7 @@ __global__ void __launch_bounds__(kKnnThreads) k_knn(KnnArgs a)
     extern __shared__ unsigned long long heap_mem[];   // [kmax][kKnnThreads]
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     unsigned long long* h = heap_mem + threadIdx.x;
-    if (!a.jobs) {
+    if (!GENERAL || !a.jobs) {
         // one tree: warp w takes positions [32 w, 32 w + 32)
         KnnSet S;
         S.nodes = a.nodes;
@@ -324,10 +450,11 @@ __global__ void __launch_bounds__(kKnnThreads) k_knn(KnnArgs a)
         S.root = 0;
         S.id_base = 0;
         S.row_base = 0;
+        S.solo = a.solo;
         S.k = a.k;
         const long long g0 = ((long long)blockIdx.x * (kKnnThreads / 32) + warp) * 32;
         if (g0 >= a.m) return;
-        knn_warp_job<DP>(a, S, g0, stage_x[warp], stage_id[warp], h);
+        knn_warp_job<DP, GENERAL>(a, S, g0, stage_x[warp], stage_id[warp], h);
         return;
     }
     // many sets: persistent warps take jobs from the device work queue
@@ -338,7 +465,7 @@ __global__ void __launch_bounds__(kKnnThreads) k_knn(KnnArgs a)
         if (j >= a.njobs) break;
         const KnnJob jb = a.jobs[j];
         const KnnSet S = a.sets[jb.set];
-        knn_warp_job<DP>(a, S, jb.pos, stage_x[warp], stage_id[warp], h);
+        knn_warp_job<DP, GENERAL>(a, S, jb.pos, stage_x[warp], stage_id[warp], h);
         __syncwarp();
     }
 }

@@ -17,6 +17,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_lib", "libpanda.so")
 
 ORDER = {"none": 0, "morton": 1, "leaf": 2}
+TRAVERSAL = {"auto": 0, "packet": 1, "per_query": 2}
 STATUS_NAMES = {0: "PANDA_OK", 1: "PANDA_ERR_INVALID_ARGUMENT", 2: "PANDA_ERR_NONFINITE_INPUT",
                 3: "PANDA_ERR_UNSUPPORTED", 4: "PANDA_ERR_OUT_OF_MEMORY", 5: "PANDA_ERR_CUDA",
                 6: "PANDA_ERR_TIMEOUT", 7: "PANDA_ERR_QUEUE_FULL", 8: "PANDA_ERR_DEPTH"}
@@ -48,6 +49,9 @@ SIGNATURES = {
     "panda_server_now_ns": ([_P], _I64),
     "panda_server_stats": ([_P, _P, _P, _P, _P], ctypes.c_int),
     "panda_server_destroy": ([_P], None),
+    "panda_tune": ([_P, _I64, _I32, _P, _I64, _I64, _I32, _P, _P], ctypes.c_int),
+    "panda_tune_lookup": ([_I32, _I64, _I32, _I64, _P], ctypes.c_int),
+    "panda_batch_set_query_params": ([_P, _P], ctypes.c_int),
     "panda_free": ([_P], None),
     "panda_tree_get_info": ([_P, _P], ctypes.c_int),
     "panda_tree_copy": ([_P, _P, _P], ctypes.c_int),
@@ -67,7 +71,8 @@ class PandaError(RuntimeError):
 
 
 class QueryParams(ctypes.Structure):
-    _fields_ = [("order", ctypes.c_int32), ("transpose_max", ctypes.c_int32)]
+    _fields_ = [("order", ctypes.c_int32), ("transpose_max", ctypes.c_int32), ("traversal", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 class TreeInfo(ctypes.Structure):
@@ -213,6 +218,38 @@ def canonical_from_raw(nodes: np.ndarray, pts: np.ndarray, d: int) -> dict:
                 perm=ids)
 
 
+class TuneResult(ctypes.Structure):
+    _fields_ = [("bucket", ctypes.c_int32), ("order", ctypes.c_int32), ("transpose_max", ctypes.c_int32),
+                ("traversal", ctypes.c_int32), ("build_ms", ctypes.c_float), ("query_ms", ctypes.c_float),
+                ("score_ms", ctypes.c_float), ("reserved2", ctypes.c_float)]
+
+
+ORDER_NAMES = {v: k for k, v in ORDER.items()}
+TRAVERSAL_NAMES = {v: k for k, v in TRAVERSAL.items()}
+
+
+def tune(points, queries_sample, k: int, m_total: int, stream=None) -> dict:
+    """panda_tune: pick bucket size, query order and scan shape by timing them."""
+    p = _as_device_points(points, "points")
+    q = _as_device_points(queries_sample, "queries")
+    r = TuneResult()
+    _check(load().panda_tune(ctypes.c_void_p(p.data_ptr()), p.shape[0], p.shape[1], ctypes.c_void_p(q.data_ptr()),
+                             q.shape[0], int(m_total), int(k), _stream_ptr(stream), ctypes.byref(r)))
+    return dict(bucket=r.bucket, order=ORDER_NAMES[r.order], transpose_max=r.transpose_max,
+                traversal=TRAVERSAL_NAMES[r.traversal], build_ms=r.build_ms, query_ms=r.query_ms,
+                score_ms=r.score_ms)
+
+
+def tune_lookup(d: int, n: int, k: int, m_total: int):
+    r = TuneResult()
+    st = load().panda_tune_lookup(int(d), int(n), int(k), int(m_total), ctypes.byref(r))
+    if st != 0:
+        return None
+    return dict(bucket=r.bucket, order=ORDER_NAMES[r.order], transpose_max=r.transpose_max,
+                traversal=TRAVERSAL_NAMES[r.traversal], build_ms=r.build_ms, query_ms=r.query_ms,
+                score_ms=r.score_ms)
+
+
 class SetDesc(ctypes.Structure):
     _fields_ = [("n_points", ctypes.c_int64), ("n_queries", ctypes.c_int64), ("k", ctypes.c_int32),
                 ("reserved", ctypes.c_int32)]
@@ -254,6 +291,10 @@ class Batch:
                                    device=dev)[:self.out_off[-1]]
         self.d2 = torch.as_tensor(_DeviceArray(dp.value, (max(self.out_off[-1], 1),), "<f4"),
                                   device=dev)[:self.out_off[-1]]
+
+    def set_query_params(self, transpose_max: int = 0, traversal: str = "auto"):
+        prm = QueryParams(ORDER["leaf"], int(transpose_max), TRAVERSAL[traversal], 0)
+        _check(load().panda_batch_set_query_params(self._h, ctypes.byref(prm)))
 
     def run(self, stream=None):
         _check(load().panda_batch_run(self._h, _stream_ptr(stream)))
@@ -374,7 +415,8 @@ def build(points, bucket: int = 32, stream=None, sync: bool = True) -> Tree:
     return t
 
 
-def knn(tree: Tree, queries, k: int, order: str = "leaf", stream=None, out=None, transpose_max: int = 0):
+def knn(tree: Tree, queries, k: int, order: str = "leaf", stream=None, out=None, transpose_max: int = 0,
+        traversal: str = "auto"):
     """Exact KNN (Algorithm 1, corrected) of every query row; enqueued on `stream`.
 
     Returns (ids int32 [m][k], d2 float32 [m][k]) CUDA tensors."""
@@ -387,7 +429,8 @@ def knn(tree: Tree, queries, k: int, order: str = "leaf", stream=None, out=None,
         d2 = torch.empty((m, k), dtype=torch.float32, device=q.device)
     else:
         ids, d2 = out
-    prm = QueryParams(ORDER[order] if isinstance(order, str) else int(order), int(transpose_max))
+    prm = QueryParams(ORDER[order] if isinstance(order, str) else int(order), int(transpose_max),
+                      TRAVERSAL[traversal], 0)
     _check(L.panda_knn_async(tree.handle, ctypes.c_void_p(q.data_ptr()), m, int(k),
                              ctypes.c_void_p(ids.data_ptr()), ctypes.c_void_p(d2.data_ptr()),
                              ctypes.byref(prm), _stream_ptr(stream)))
@@ -405,7 +448,7 @@ def knn_visits(tree: Tree, queries, k: int, order: str = "leaf", stream=None, tr
     d2 = torch.empty((m, k), dtype=torch.float32, device=q.device)
     vis = torch.zeros((m, 2), dtype=torch.int32, device=q.device)
     stats = torch.zeros(8, dtype=torch.int64, device=q.device)
-    prm = QueryParams(ORDER[order], int(transpose_max))
+    prm = QueryParams(ORDER[order], int(transpose_max), 0, 0)
     _check(L.panda_knn_visits(tree.handle, ctypes.c_void_p(q.data_ptr()), m, int(k),
                               ctypes.c_void_p(ids.data_ptr()), ctypes.c_void_p(d2.data_ptr()),
                               ctypes.c_void_p(vis.data_ptr()), ctypes.c_void_p(stats.data_ptr()),
@@ -465,7 +508,7 @@ def knn_host(tree: Tree, queries: np.ndarray, k: int, order: str = "leaf", strea
         d2 = np.empty((m, k), np.float32)
     else:
         ids, d2 = out
-    prm = QueryParams(ORDER[order], 0)
+    prm = QueryParams(ORDER[order], 0, 0, 0)
     _check(L.panda_knn_host(tree.handle, q.ctypes.data_as(ctypes.c_void_p), m, int(k),
                             ids.ctypes.data_as(ctypes.c_void_p), d2.ctypes.data_as(ctypes.c_void_p),
                             ctypes.byref(prm), _stream_ptr(stream)))

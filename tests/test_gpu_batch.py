@@ -89,6 +89,13 @@ def test_batch_matches_single_trees_and_replays(P):
     torch.cuda.synchronize()
     batch.status()
     check_against_single(P, batch, sets2, oracle_sets=(1,))
+    # every set forced to each traversal shape: still exact (replays the same graph)
+    for trav in ("packet", "per_query"):
+        batch.set_query_params(0, trav)
+        batch.run()
+        torch.cuda.synchronize()
+        batch.status()
+        check_against_single(P, batch, sets2)
     batch.free()
 
 

@@ -31,9 +31,9 @@ def dev(x):
     return torch.from_numpy(np.ascontiguousarray(x, dtype=np.float32)).cuda()
 
 
-def gpu_knn(P, tree, q, k, order="leaf", transpose_max=0):
+def gpu_knn(P, tree, q, k, order="leaf", transpose_max=0, traversal="auto"):
     import torch
-    ids, d2 = P.knn(tree, dev(q), k, order=order, transpose_max=transpose_max)
+    ids, d2 = P.knn(tree, dev(q), k, order=order, transpose_max=transpose_max, traversal=traversal)
     torch.cuda.synchronize()
     return ids.cpu().numpy(), d2.cpu().numpy()
 
@@ -57,7 +57,10 @@ def full_parity(P, pts, q, k, B, orders=("leaf",), brute_rows=None, shapes=(0, -
         ids, d2 = gpu_knn(P, t, q, k, order)
         assert_same_knn(ids, d2, eids, ed2)
     for shape in shapes:     # both leaf-scan shapes (lanes = queries, lanes = points)
-        ids, d2 = gpu_knn(P, t, q, k, orders[0], transpose_max=shape)
+        ids, d2 = gpu_knn(P, t, q, k, orders[0], transpose_max=shape, traversal="packet")
+        assert_same_knn(ids, d2, eids, ed2)
+    for order in orders:     # each lane walking its own query
+        ids, d2 = gpu_knn(P, t, q, k, order, traversal="per_query")
         assert_same_knn(ids, d2, eids, ed2)
     if brute_rows is not None:
         bi, bd = oracle.brute_knn(pts, q, k, rows=brute_rows)
@@ -184,6 +187,26 @@ def test_cosmology_self_full_size(P):
     assert np.all(ids[nodup, 0] == np.flatnonzero(nodup))
     ot = oracle.build(w.points, w.bucket)
     treecheck.assert_same_tree(g, ot.export())
+
+
+def test_sparse_queries_full_size_tree(P):
+    """Few queries against the 2^24-point tree (the automatic choice walks each
+    query on its own lane): equal to the packet traversal and, on sampled rows,
+    to exhaustive search."""
+    import torch
+    w = workloads.cosmology_self()
+    q = workloads.cosmology_points(60_000, seed=77)
+    t = P.build(dev(w.points), w.bucket)
+    res = {}
+    for trav in ("auto", "per_query", "packet"):
+        ids, d2 = P.knn(t, dev(q), 16, traversal=trav)
+        torch.cuda.synchronize()
+        res[trav] = (ids.cpu().numpy(), d2.cpu().numpy())
+    assert_same_knn(*res["auto"], *res["packet"])
+    assert_same_knn(*res["per_query"], *res["packet"])
+    rows = np.random.default_rng(3).choice(q.shape[0], 300, replace=False)
+    bi, bd = oracle.brute_knn(w.points, q, 16, rows=rows)
+    assert_same_knn(res["auto"][0][rows], res["auto"][1][rows], bi, bd)
 
 
 def test_features_10d_full_size(P):

@@ -34,29 +34,32 @@ def test_mixed_requests_equal_alone(P):
     rng = np.random.default_rng(5)
     pts_a = torch.from_numpy(workloads.cosmology_points(200_000, seed=50, halos=30)).cuda()
     pts_b = torch.from_numpy(workloads.plasma_points(150_000, seed=51)).cuda()
+    pts_c = torch.from_numpy(workloads.cosmology_points(30_000, seed=52, halos=5)).cuda()
     srv = P.Server(max_batch_queries=40_000)
-    ta, tb = srv.add_tree(pts_a), srv.add_tree(pts_b)
-    ref_a, ref_b = P.build(pts_a, 32), P.build(pts_b, 32)
+    tids = [srv.add_tree(pts_a), srv.add_tree(pts_b), srv.add_tree(pts_c)]
+    refs = [P.build(pts_a, 32), P.build(pts_b, 32), P.build(pts_c, 32)]
     todo = []
-    for i in range(80):
-        tree = int(rng.integers(0, 2))
+    for i in range(90):
+        # requests of the small tree c are often dense (more than n/4 queries:
+        # packet traversal), the others sparse (a lane per query)
+        tree = int(rng.integers(0, 3))
         m = int(np.floor(np.exp(rng.uniform(0, np.log(20_001)))))
         k = int(rng.choice([1, 8, 32]))
-        q = (workloads.cosmology_points(m, seed=1000 + i, halos=30) if tree == 0
-             else workloads.plasma_points(m, seed=1000 + i))
+        q = (workloads.plasma_points(m, seed=1000 + i) if tree == 1
+             else workloads.cosmology_points(m, seed=1000 + i, halos=30 if tree == 0 else 5))
         qd = torch.from_numpy(q).cuda()
         out = (torch.empty((m, k), dtype=torch.int32, device="cuda"),
                torch.empty((m, k), dtype=torch.float32, device="cuda"))
         todo.append((tree, qd, k, out))
     torch.cuda.synchronize()
-    reqs = [(srv.submit([ta, tb][tree], qd, k, out), tree, qd, k, out) for tree, qd, k, out in todo]
+    reqs = [(srv.submit(tids[tree], qd, k, out), tree, qd, k, out) for tree, qd, k, out in todo]
     for rid, tree, qd, k, out in reqs:
         srv.wait(rid, 60)
-        ri, rd = alone(P, [ref_a, ref_b][tree], qd, k)
+        ri, rd = alone(P, refs[tree], qd, k)
         assert torch.equal(out[0], ri)
         assert torch.equal(out[1].view(torch.int32), rd.view(torch.int32))
     st = srv.stats()
-    assert st["requests"] == 80 and st["batches"] < 80          # requests were coalesced
+    assert st["requests"] == 90 and st["batches"] < 90          # requests were coalesced
     batches = {srv.times(r[0])[2] for r in reqs}
     assert len(batches) == st["batches"]
     srv.close()

@@ -1,0 +1,31 @@
+"""Autotuner: picks a valid (bucket, order, traversal, scan shape) by timing, caches it, and
+the tuned configuration returns exactly the default configuration's results
+(none of the knobs may change an answer)."""
+import pytest
+
+from paper_1607_08220_gb300 import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+def test_tune_choice_is_exact_and_cached():
+    import torch
+    assert torch.cuda.is_available(), "needs a CUDA device"
+    from paper_1607_08220_gb300 import build_ext, panda as P
+    build_ext.build()
+    P.load()
+    pts = torch.from_numpy(workloads.cosmology_points(200_000, seed=70, halos=30)).cuda()
+    q = torch.from_numpy(workloads.cosmology_points(30_000, seed=71, halos=30)).cuda()
+    r = P.tune(pts, q[:20_000], k=10, m_total=200_000)
+    assert r["bucket"] in (16, 32, 64) and r["order"] in ("none", "morton", "leaf")
+    assert r["traversal"] in ("packet", "per_query")
+    assert r["transpose_max"] in ((-1, 4, 8, 12, 16, 32) if r["traversal"] == "packet" else (0,))
+    assert r["score_ms"] > 0 and r["score_ms"] >= r["build_ms"]
+    assert P.tune_lookup(3, 200_000, 10, 200_000) == r
+    assert P.tune_lookup(3, 200_000, 11, 200_000) is None
+    tuned = P.build(pts, r["bucket"])
+    ti, td = P.knn(tuned, q, 10, order=r["order"], transpose_max=r["transpose_max"], traversal=r["traversal"])
+    default = P.build(pts, 32)
+    di, dd = P.knn(default, q, 10)
+    torch.cuda.synchronize()
+    assert torch.equal(ti, di) and torch.equal(td.view(torch.int32), dd.view(torch.int32))
