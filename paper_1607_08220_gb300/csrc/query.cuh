@@ -6,8 +6,12 @@
 // the squared distance from its query to the node's tight box, and the node
 // is skipped only when every lane's bound is strictly greater than its current
 // k-th distance (corrections C1, C3).  Inner nodes push the far child first
-// and the near child last (Algorithm 1 lines 20-24); the near side is the one
-// the majority of the lanes that need the node fall on.
+// and the near child last, as Algorithm 1 does; the near side is the one the
+// majority of the lanes that need the node fall on.
+//
+// Sparse query sets (fewer queries than a quarter of the points) leave the 32
+// queries of a warp far apart, and a shared stack would walk the union of
+// their paths; there each lane walks its own query instead (knn_lane_solo).
 //
 // A leaf bucket is staged once into shared memory, structure-of-arrays, and
 // scanned (Sec. III-C: the bucket scan is the SIMD-friendly part) in one of
