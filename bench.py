@@ -46,6 +46,10 @@ def parse():
                     default="cosmology_self")
     ap.add_argument("--duration", type=float, default=1.0, help="seconds of the served request stream")
     ap.add_argument("--nsets", type=int, default=512, help="sets of the batched workload")
+    ap.add_argument("--rate-factors", type=lambda v: [float(x) for x in v.split(",") if x],
+                    default=[0.5, 1.0, 1.25, 1.5, 2.0],
+                    help="served: replay the stream at these multiples of its arrival rate")
+    ap.add_argument("--slo-ms", type=float, default=100.0, help="served: p99 latency target of the sweep")
     ap.add_argument("--order", choices=["leaf", "morton", "none"], default="leaf")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -595,6 +599,29 @@ def run_served(args):
     st = srv.stats()
     served = {"value": m_total / span_s, "unit": UNIT, **_latency_stats(lat), "batches": st["batches"],
               "requests_per_batch": st["requests"] / max(st["batches"], 1), "span_s": span_s}
+    # rate sweep: the same requests (both trees resident) with arrival times
+    # compressed by each factor; a rate is sustained while p99 <= the SLO
+    sweep = []
+    for f in args.rate_factors:
+        t0s = srv.now_ns() + 20_000_000
+        srids = []
+        for i, r in enumerate(reqs):
+            due = t0s + int(r["t"] / f * 1e9)
+            while srv.now_ns() < due:
+                pass
+            srids.append(srv.submit(tree_ids[r["tree"]], qdev[i], r["k"], outs[i]))
+        for rid in srids:
+            srv.wait(rid, 600)
+        sl = [(srv.times(rid)[1] - (t0s + int(r["t"] / f * 1e9))) / 1e6 for rid, r in zip(srids, reqs)]
+        sspan = (max(srv.times(rid)[1] for rid in srids) - t0s) / 1e9
+        st_ = _latency_stats(sl)
+        sweep.append({"requests_per_s": len(reqs) / (args.duration / f), "offered_queries_per_s":
+                      m_total / (args.duration / f), "queries_per_s": m_total / sspan,
+                      "p50_ms": st_["p50_ms"], "p99_ms": st_["p99_ms"]})
+    ok = [x["requests_per_s"] for x in sweep if x["p99_ms"] <= args.slo_ms]
+    served["rate_sweep"] = sweep
+    served["slo_p99_ms"] = args.slo_ms
+    served["sustained_requests_per_s"] = max(ok) if ok else None
     # capacity: every request submitted at once
     tb = srv.now_ns()
     brids = [srv.submit(tree_ids[r["tree"]], qdev[i], r["k"], outs[i]) for i, r in enumerate(reqs)]

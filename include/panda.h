@@ -78,7 +78,8 @@ typedef struct panda_query_params {
                                queries; 0 = default (12), 32 = always the former,
                                -1 = always the latter.  Never changes results. */
     int32_t traversal;      /* PANDA_TRAVERSAL_*: 0 = automatic (per-query when the
-                               queries are sparse: fewer than n/4), never changes results */
+                               queries are sparse, fewer than n/4, and d <= 4), never
+                               changes results */
     int32_t reserved;
 } panda_query_params;
 
@@ -179,7 +180,7 @@ panda_status panda_batch_offsets(const panda_batch* batch, int64_t* point_off, i
                                  int64_t* out_off);
 /* Query parameters of the batch's traversal (order must be PANDA_ORDER_LEAF
  * or params NULL for defaults).  traversal AUTO chooses per set (per-query
- * when the set has fewer than n/4 queries); PACKET or PER_QUERY applies to
+ * when the set has fewer than n/4 queries and d <= 4); PACKET or PER_QUERY applies to
  * every set.  After a run this waits for the whole device and drops the
  * captured graph; the next panda_batch_run captures it again. */
 panda_status panda_batch_set_query_params(panda_batch* batch, const panda_query_params* params);

@@ -246,7 +246,7 @@ panda_status panda_batch_create(const panda_set_desc* sets, int32_t nsets, int32
         S.id_base = (int)b->poff[s];
         S.k = b->ks[s];
         S.row_base = (int)b->qoff[s];
-        S.solo = 4 * b->nq[s] < b->np[s];
+        S.solo = prefer_per_query(b->nq[s], b->np[s], d);
         for (long long p = 0; p < b->nq[s]; p += 32) hj.push_back(KnnJob{s, (int)p});
     }
     b->njobs = (int)hj.size();

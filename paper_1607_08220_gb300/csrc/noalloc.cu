@@ -171,6 +171,6 @@ extern "C" panda_status panda_knn_noalloc(const panda_tree* t, const float* quer
     ka.d = t->d;
     ka.k = k;
     ka.transpose_max = 12;
-    ka.solo = 4 * m < t->n;
+    ka.solo = prefer_per_query(m, t->n, t->d);
     return launch_traversal(ka, t->dp, s);
 }

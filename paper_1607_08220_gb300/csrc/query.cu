@@ -272,7 +272,9 @@ panda_status knn_query(const panda_tree* t, const float* queries, int64_t m, int
     ka.transpose_max = (params && params->transpose_max != 0) ? params->transpose_max : 12;
     {
         const int tr = params ? params->traversal : PANDA_TRAVERSAL_AUTO;
-        ka.solo = tr == PANDA_TRAVERSAL_PER_QUERY ? 1 : tr == PANDA_TRAVERSAL_PACKET ? 0 : (4 * m < t->n);
+        ka.solo = tr == PANDA_TRAVERSAL_PER_QUERY ? 1
+                  : tr == PANDA_TRAVERSAL_PACKET  ? 0
+                                                  : prefer_per_query(m, t->n, t->d);
     }
     ka.d = t->d;
     ka.k = k;

@@ -78,6 +78,12 @@ int num_sms();
 // Build and query entry points implemented in build.cu / query.cu.
 panda_status build_tree(const float* points, int64_t n, int32_t d, int32_t bucket,
                         cudaStream_t stream, panda_tree** out);
+// Automatic traversal shape: each lane walks its own query when the queries
+// are sparse (fewer than a quarter of the points) in low dimension (d <= 4).
+// At d = 10 the search regions of even distant queries overlap, and the
+// packet traversal was faster at every query count measured.
+inline bool prefer_per_query(long long m, long long n, int d) { return d <= 4 && 4 * m < n; }
+
 panda_status knn_query(const panda_tree* t, const float* queries, int64_t m, int32_t k,
                        int32_t* ids, float* d2, const panda_query_params* params,
                        cudaStream_t stream, unsigned* host_err, int32_t* visits = nullptr,

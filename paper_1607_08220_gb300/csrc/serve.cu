@@ -170,7 +170,7 @@ panda_status enqueue_batch(Server* S, const std::vector<Request*>& batch, InFlig
         K.id_base = 0;
         K.k = R->k;
         K.row_base = (int)m_total;
-        K.solo = 4 * R->m < t->n;
+        K.solo = prefer_per_query(R->m, t->n, t->d);
         for (long long p = 0; p < R->m; p += 32) jobs.push_back(KnnJob{r, (int)p});
         m_total += R->m;
         kmax = std::max(kmax, R->k);
