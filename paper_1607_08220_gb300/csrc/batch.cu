@@ -50,6 +50,7 @@ struct panda_batch {
     int64_t kernels_per_run = 0;
     int transpose_max = 12;
     int traversal = PANDA_TRAVERSAL_AUTO;
+    int any_solo = 0;   // some set takes the per-query traversal
     std::vector<void*> owned;
 };
 
@@ -126,6 +127,7 @@ panda_status batch_enqueue(panda_batch* b, cudaStream_t s)
     ka.d = b->d;
     ka.k = b->kmax;
     ka.transpose_max = b->transpose_max;
+    ka.solo = b->any_solo;
     return launch_multi(ka, padded_dim(b->d), s);
 }
 
@@ -247,6 +249,7 @@ panda_status panda_batch_create(const panda_set_desc* sets, int32_t nsets, int32
         S.k = b->ks[s];
         S.row_base = (int)b->qoff[s];
         S.solo = prefer_per_query(b->nq[s], b->np[s], d);
+        b->any_solo |= S.solo;
         for (long long p = 0; p < b->nq[s]; p += 32) hj.push_back(KnnJob{s, (int)p});
     }
     b->njobs = (int)hj.size();
@@ -317,15 +320,19 @@ panda_status panda_batch_set_query_params(panda_batch* b, const panda_query_para
     }
     b->transpose_max = (params && params->transpose_max != 0) ? params->transpose_max : 12;
     b->traversal = params ? params->traversal : PANDA_TRAVERSAL_AUTO;
-    if (b->traversal != PANDA_TRAVERSAL_AUTO) {
-        // rewrite the set descriptors with the requested traversal shape
-        std::vector<KnnSet> hs(b->nsets);
-        PANDA_CUDA(cudaMemcpy(hs.data(), b->d_sets, b->nsets * sizeof(KnnSet), cudaMemcpyDeviceToHost),
-                   "panda_batch_set_query_params");
-        for (KnnSet& S : hs) S.solo = b->traversal == PANDA_TRAVERSAL_PER_QUERY;
-        PANDA_CUDA(cudaMemcpy(b->d_sets, hs.data(), b->nsets * sizeof(KnnSet), cudaMemcpyHostToDevice),
-                   "panda_batch_set_query_params");
+    // rewrite the set descriptors with the requested traversal shape
+    std::vector<KnnSet> hs(b->nsets);
+    PANDA_CUDA(cudaMemcpy(hs.data(), b->d_sets, b->nsets * sizeof(KnnSet), cudaMemcpyDeviceToHost),
+               "panda_batch_set_query_params");
+    b->any_solo = 0;
+    for (int s = 0; s < b->nsets; s++) {
+        hs[s].solo = b->traversal == PANDA_TRAVERSAL_PER_QUERY ? 1
+                     : b->traversal == PANDA_TRAVERSAL_PACKET  ? 0
+                                                               : prefer_per_query(b->nq[s], b->np[s], b->d);
+        b->any_solo |= hs[s].solo;
     }
+    PANDA_CUDA(cudaMemcpy(b->d_sets, hs.data(), b->nsets * sizeof(KnnSet), cudaMemcpyHostToDevice),
+               "panda_batch_set_query_params");
     return PANDA_OK;
 }
 

@@ -539,26 +539,34 @@ __global__ void k_tilecount(BuildArgs a, int L)
 
 // One block: per-tile left offsets, children creation (next level or subtree
 // stage), node headers of this level, tile plan of the next level.
+// Left-count offsets of every node's tiles (exclusive scan of the per-tile
+// left counts within the node), one warp per node over the whole grid.
+__global__ void k_tileoff(BuildArgs a, int L)
+{
+    const int cur = L & 1;
+    const int A = a.cnt[kCntActive0 + cur];
+    const int lane = threadIdx.x & 31;
+    const int ai = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (ai >= A) return;
+    const int tb = min(a.tile_base[cur][ai], a.tile_cap);
+    const int te = min(a.tile_base[cur][ai + 1], a.tile_cap);
+    int running = 0;
+    for (int j0 = tb; j0 < te; j0 += 32) {
+        int j = j0 + lane;
+        int v = j < te ? a.tleft[j] : 0;
+        int incl = warp_incl_scan(v);
+        if (j < te) a.tleftoff[j] = running + incl - v;
+        running += __shfl_sync(kFull, incl, 31);
+    }
+    if (lane == 0 && running != a.nleft[ai]) atomicOr(a.err, kErrInternal);
+}
+
 __global__ void k_children(BuildArgs a, int L)
 {
     __shared__ int sh[33];
     __shared__ int s_next, s_small;
     const int cur = L & 1, nxt = cur ^ 1;
     const int A = a.cnt[kCntActive0 + cur];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int ai = warp; ai < A; ai += nw) {
-        const int tb = min(a.tile_base[cur][ai], a.tile_cap);
-        const int te = min(a.tile_base[cur][ai + 1], a.tile_cap);
-        int running = 0;
-        for (int j0 = tb; j0 < te; j0 += 32) {
-            int j = j0 + lane;
-            int v = j < te ? a.tleft[j] : 0;
-            int incl = warp_incl_scan(v);
-            if (j < te) a.tleftoff[j] = running + incl - v;
-            running += __shfl_sync(kFull, incl, 31);
-        }
-        if (lane == 0 && running != a.nleft[ai]) atomicOr(a.err, kErrInternal);
-    }
     const int base_id = a.cnt[kCntNodes];
     if (threadIdx.x == 0) {
         s_next = 0;
@@ -787,6 +795,7 @@ __device__ void write_node(const BuildArgs& a, int node, int4 hdr, const float* 
 // the global counter 64 ids at a time; ids left in a pool are holes in the
 // node table that nothing references.
 constexpr int kIdChunk = 64;
+constexpr int kSubtreeMaxWarps = 32;   // warps of the one k_subtree block per SM
 
 __global__ void k_subtree(BuildArgs a, int wbytes)
 {
@@ -1139,8 +1148,27 @@ panda_status configure_kernels()
 
 struct Plan {
     int T, act_cap, tile_cap, small_cap, lvl_stride, max_levels;
+    int sub_warps;   // warps of the k_subtree block (one block per SM)
     long long node_cap;
 };
+
+// Warps of the persistent k_subtree block: as many as the shared memory (one
+// node of <= T points per warp) and the register file allow, checked with the
+// occupancy calculator (register allocation rounds warps up).  Called before
+// any enqueue, so a captured build needs no query.
+panda_status subtree_warps(int d, int T, int* out)
+{
+    const int wb = (int)warp_bytes(d, T);
+    int w = std::max(1, std::min(kSubtreeMaxWarps, (227 * 1024) / wb));
+    for (; w > 1; w--) {
+        int nb = 0;
+        PANDA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_subtree, w * 32, (size_t)w * wb),
+                   "k_subtree occupancy");
+        if (nb >= 1) break;
+    }
+    *out = w;
+    return PANDA_OK;
+}
 
 }  // namespace
 
@@ -1241,7 +1269,7 @@ panda_status enqueue_start(BuildState& S, cudaStream_t stream, PhaseTimer& timer
     return PANDA_OK;
 }
 
-// The six kernels of one data-parallel level pass.
+// The seven kernels of one data-parallel level pass.
 panda_status enqueue_level(BuildState& S, int L, cudaStream_t stream, PhaseTimer& timer)
 {
     BuildArgs& a = S.a;
@@ -1261,6 +1289,8 @@ panda_status enqueue_level(BuildState& S, int L, cudaStream_t stream, PhaseTimer
     PANDA_LAUNCHED("k_select");
     k_tilecount<<<(tcap + 7) / 8, 256, 0, stream>>>(a, L);
     PANDA_LAUNCHED("k_tilecount");
+    k_tileoff<<<(acap + 7) / 8, 256, 0, stream>>>(a, L);
+    PANDA_LAUNCHED("k_tileoff");
     k_children<<<1, 1024, 0, stream>>>(a, L);
     PANDA_LAUNCHED("k_children");
     timer.begin("level.partition");
@@ -1276,7 +1306,7 @@ panda_status enqueue_finish(BuildState& S, int nlevels, cudaStream_t stream, Pha
     const int sms = num_sms();
     timer.begin("subtree");
     const int wb = (int)warp_bytes(a.d, S.pl.T);
-    const int wpb = std::max(1, std::min(8, (227 * 1024) / wb));
+    const int wpb = S.pl.sub_warps;
     k_subtree<<<sms, wpb * 32, (size_t)wpb * wb, stream>>>(a, wb);
     PANDA_LAUNCHED("k_subtree");
     timer.begin("boxes");
@@ -1405,12 +1435,16 @@ panda_status forest_create(const long long* set_sizes, int nsets, int d, int buc
     Plan& pl = S->pl;
     pl.T = subtree_threshold(d, bucket);
     t->threshold = pl.T;
+    if ((st = subtree_warps(d, pl.T, &pl.sub_warps)) != PANDA_OK) {
+        delete S;
+        return st;
+    }
     pl.act_cap = (int)(n / (pl.T + 1)) + 1;
     pl.tile_cap = (int)(n / kTile) + 2 * pl.act_cap + 4;
     pl.small_cap = nsets + 8 * pl.act_cap + 64;
     pl.lvl_stride = pl.act_cap;
     pl.max_levels = kMaxDepth + 1;
-    pl.node_cap = 2LL * n + 8 + nsets + (long long)num_sms() * 8 * kIdChunk;
+    pl.node_cap = 2LL * n + 8 + nsets + (long long)num_sms() * kSubtreeMaxWarps * kIdChunk;
     S->max_set = max_set;
     t->node_cap = pl.node_cap;
     void *pn = nullptr, *pp = nullptr, *po = nullptr;
@@ -1517,13 +1551,14 @@ panda_status build_tree(const float* points, int64_t n64, int32_t d, int32_t buc
     Plan pl;
     pl.T = subtree_threshold(d, bucket);
     t->threshold = pl.T;
+    if ((st = subtree_warps(d, pl.T, &pl.sub_warps)) != PANDA_OK) return st;
     pl.act_cap = n / (pl.T + 1) + 1;
     pl.tile_cap = n / kTile + 2 * pl.act_cap + 4;
     pl.small_cap = 4 * pl.act_cap + 16;
     pl.lvl_stride = pl.act_cap;
     pl.max_levels = kMaxDepth + 1;
     // holes: each subtree warp may leave up to kIdChunk unused ids
-    const long long hole_slack = (long long)num_sms() * 8 * kIdChunk;
+    const long long hole_slack = (long long)num_sms() * kSubtreeMaxWarps * kIdChunk;
     const long long node_max = 2LL * n + 8 + hole_slack;
     pl.node_cap = 4LL * n / bucket + 8LL * pl.act_cap + 1024 + hole_slack;
     pl.node_cap = std::min<long long>(pl.node_cap, node_max);

@@ -8,38 +8,85 @@
 
 namespace panda {
 
-template <int DP>
-panda_status configure_knn()
+template <int DP, bool MULTI, bool SOLO>
+panda_status configure_knn_variant()
 {
-    static bool configured = false;
-    if (!configured) {
-        PANDA_CUDA(cudaFuncSetAttribute(k_knn<DP, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        kMaxK * kKnnThreads * 8),
-                   "configure k_knn");
-        PANDA_CUDA(cudaFuncSetAttribute(k_knn<DP, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        kMaxK * kKnnThreads * 8),
-                   "configure k_knn");
-        configured = true;
+    PANDA_CUDA(cudaFuncSetAttribute(k_knn<DP, MULTI, SOLO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    kMaxK * kKnnThreads * 8),
+               "configure k_knn");
+    return PANDA_OK;
+}
+
+// Resident blocks per SM of the multi-set kernel, [solo][k], filled by
+// configure_knn (before any graph capture, so a captured launch needs no query).
+template <int DP>
+int (&multi_blocks_per_sm())[2][kMaxK + 1]
+{
+    static int t[2][kMaxK + 1];
+    return t;
+}
+
+template <int DP, bool SOLO>
+panda_status fill_multi_blocks()
+{
+    for (int k = 1; k <= kMaxK; k++) {
+        int v = 0;
+        PANDA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_knn<DP, true, SOLO>, kKnnThreads,
+                                                                 (size_t)k * kKnnThreads * 8),
+                   "k_knn occupancy");
+        multi_blocks_per_sm<DP>()[SOLO ? 1 : 0][k] = v > 0 ? v : 1;
     }
     return PANDA_OK;
 }
 
 template <int DP>
+panda_status configure_knn()
+{
+    static bool configured = false;
+    if (!configured) {
+        panda_status st = configure_knn_variant<DP, false, false>();
+        if (st == PANDA_OK) st = configure_knn_variant<DP, false, true>();
+        if (st == PANDA_OK) st = configure_knn_variant<DP, true, false>();
+        if (st == PANDA_OK) st = configure_knn_variant<DP, true, true>();
+        if (st == PANDA_OK) st = fill_multi_blocks<DP, false>();
+        if (st == PANDA_OK) st = fill_multi_blocks<DP, true>();
+        if (st != PANDA_OK) return st;
+        configured = true;
+    }
+    return PANDA_OK;
+}
+
+// Persistent launch of the multi-set kernel: as many blocks as can be resident.
+template <int DP, bool SOLO>
+panda_status launch_knn_multi(const KnnArgs& a, size_t heap_bytes, cudaStream_t s)
+{
+    const int per_sm = multi_blocks_per_sm<DP>()[SOLO ? 1 : 0][std::min(std::max(a.k, 1), kMaxK)];
+    const long long blocks = (long long)num_sms() * per_sm;
+    k_knn<DP, true, SOLO><<<(unsigned)blocks, kKnnThreads, heap_bytes, s>>>(a);
+    PANDA_LAUNCHED("k_knn");
+    return PANDA_OK;
+}
+
+// a.jobs selects the multi-set kernel; a.solo = 1 compiles in the per-query
+// traversal (for a multi-set launch: some set has its solo flag set).
+template <int DP>
 panda_status launch_knn_dp(const KnnArgs& a, cudaStream_t s)
 {
     panda_status st = configure_knn<DP>();
     if (st != PANDA_OK) return st;
-    // one launch per tree: one warp per 32 queries; many sets: persistent
-    // warps (8 blocks per SM) draining the job queue
-    const long long warps = (a.m + 31) / 32;
-    const long long blocks = a.jobs ? (long long)num_sms() * 8
-                                    : (warps + kKnnThreads / 32 - 1) / (kKnnThreads / 32);
-    if (blocks <= 0) return PANDA_OK;
     const size_t heap_bytes = (size_t)a.k * kKnnThreads * 8;
-    if (a.jobs || a.solo)
-        k_knn<DP, true><<<(unsigned)blocks, kKnnThreads, heap_bytes, s>>>(a);
+    if (a.jobs) {
+        if (a.njobs <= 0) return PANDA_OK;
+        return a.solo ? launch_knn_multi<DP, true>(a, heap_bytes, s) : launch_knn_multi<DP, false>(a, heap_bytes, s);
+    }
+    // one launch per tree: one warp per 32 queries
+    const long long warps = (a.m + 31) / 32;
+    const long long blocks = (warps + kKnnThreads / 32 - 1) / (kKnnThreads / 32);
+    if (blocks <= 0) return PANDA_OK;
+    if (a.solo)
+        k_knn<DP, false, true><<<(unsigned)blocks, kKnnThreads, heap_bytes, s>>>(a);
     else
-        k_knn<DP, false><<<(unsigned)blocks, kKnnThreads, heap_bytes, s>>>(a);
+        k_knn<DP, false, false><<<(unsigned)blocks, kKnnThreads, heap_bytes, s>>>(a);
     PANDA_LAUNCHED("k_knn");
     return PANDA_OK;
 }

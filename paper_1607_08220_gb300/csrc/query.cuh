@@ -33,10 +33,21 @@
 
 namespace panda {
 
-// One query set against one tree (a request of the served form, or one set of
-// a batched forest).  Rows of `queries` are the set's queries; `perm` (may be
-// null) lists them in traversal order as row_base + row; ids written are
-// stored ids - id_base.
+// One request of a served batch: its queries are batch rows
+// [row_begin, row_begin + m) and its results go to ids / d2 ([m][k]).
+struct KnnReq {
+    const float* queries;
+    int* ids;
+    float* d2;
+    int k, row_begin;
+};
+
+// One query set against one tree (one set of a batched forest, or all the
+// requests of a served batch on one tree).  Rows of `queries` are the set's
+// queries; `perm` (may be null) lists them in traversal order as row_base +
+// row; ids written are stored ids - id_base.  With `reqs` the set spans
+// several requests: perm lists batch rows, and each lane finds its request
+// (queries, k, outputs) by row.
 struct KnnSet {
     const float4* nodes;
     const float4* pts;
@@ -48,7 +59,8 @@ struct KnnSet {
     long long m;
     int root, id_base, k, row_base;
     int solo;   // 1: each lane walks its own query (sparse query sets); 0: warp packets
-    int pad;
+    int nreq;   // entries of reqs (0: the set is one request, fields above)
+    const KnnReq* reqs;
 };
 // A warp job: traversal positions [pos, pos + 32) of one set.
 struct KnnJob {
@@ -74,7 +86,7 @@ struct KnnArgs {
     long long npts;
     int d, k;
     int transpose_max;    // use the transposed scan when at most this many lanes need a bucket
-    int solo;             // single-tree launch: traversal shape (see KnnSet::solo)
+    int solo;             // single tree: per-query traversal; many sets: some set has solo set
 };
 
 constexpr unsigned long long kKeyEmpty = (0x7f800000ull << 32) | 0xffffffffull;
@@ -215,8 +227,9 @@ __device__ __forceinline__ void knn_lane_solo(const KnnArgs& a, const KnnSet& S,
 
 // Traversal of one warp job: positions [g0, g0 + 32) of set S.  SOLO_OK
 // compiles the per-query traversal in (taken when S.solo is set); without it
-// the kernel holds the packet traversal alone and keeps its registers.
-template <int DP, bool SOLO_OK>
+// the kernel holds the packet traversal alone and keeps its registers.  MULTI
+// compiles in the per-lane request lookup of sets that span several requests.
+template <int DP, bool SOLO_OK, bool MULTI>
 __device__ __forceinline__ void knn_warp_job(const KnnArgs& a, const KnnSet& S, long long g0,
                                              float (*sx)[32], int* sid, unsigned long long* h)
 {
@@ -227,15 +240,32 @@ __device__ __forceinline__ void knn_warp_job(const KnnArgs& a, const KnnSet& S, 
     const bool valid = pos < S.m;
     int qi = 0;
     if (valid) qi = S.perm ? S.perm[pos] - S.row_base : (int)pos;
+    const float* qsrc = S.queries;
+    int* out_ids = S.ids;
+    float* out_d2 = S.d2;
+    int K = S.k;
+    if (MULTI && S.nreq > 0 && valid) {
+        // the request holding batch row qi: the last one starting at or before it
+        int lo = 0, hi = S.nreq - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (S.reqs[mid].row_begin <= qi) lo = mid; else hi = mid - 1;
+        }
+        const KnnReq R = S.reqs[lo];
+        qsrc = R.queries;
+        out_ids = R.ids;
+        out_d2 = R.d2;
+        K = R.k;
+        qi -= R.row_begin;
+    }
     float q[DP];
     bool finite = true;
 #pragma unroll
     for (int k = 0; k < DP; k++) {
-        q[k] = (valid && k < a.d) ? S.queries[(long long)qi * a.d + k] : 0.0f;
+        q[k] = (valid && k < a.d) ? qsrc[(long long)qi * a.d + k] : 0.0f;
         finite &= (__float_as_uint(q[k]) & 0x7f800000u) != 0x7f800000u;
     }
     if (!finite) atomicOr(a.err, kErrNonfinite);
-    const int K = S.k;
     for (int i = 0; i < K; i++) h[i * kKnnThreads] = kKeyEmpty;
     // k-th best key so far (the heap root); invalid lanes never accept anything
     unsigned long long kth = valid ? kKeyEmpty : 0ull;
@@ -416,8 +446,8 @@ __device__ __forceinline__ void knn_warp_job(const KnnArgs& a, const KnnSet& S, 
     }
     if (valid) {
         // empty the heap in descending order into positions k-1 .. 0
-        int* oi = S.ids + (long long)qi * K;
-        float* od = S.d2 + (long long)qi * K;
+        int* oi = out_ids + (long long)qi * K;
+        float* od = out_d2 + (long long)qi * K;
         for (int sz = K; sz > 0; sz--) {
             const unsigned long long top = h[0];
             const int id = (int)(unsigned)(top & 0xffffffffull);
@@ -429,24 +459,31 @@ __device__ __forceinline__ void knn_warp_job(const KnnArgs& a, const KnnSet& S, 
 }
 
 
-// Resident blocks per SM the register allocation must allow.  The packet
-// kernel at low dimension fits 32 registers with a few bytes of spill and
-// then runs at full occupancy (measured 8% faster on 3-D self-KNN than at 45
-// registers and 10 blocks); wider points keep about 48 registers.  The
-// general kernel keeps 64 registers (no spill of its per-lane stacks).
-constexpr int knn_min_blocks(int dp, bool general) { return general ? 8 : (dp <= 4 ? 16 : 10); }
+// Resident blocks per SM the register allocation must allow.  The one-tree
+// packet traversal at low dimension fits 32 registers with a few bytes of
+// spill and then runs at full occupancy (measured 8% faster on 3-D self-KNN
+// than at 45 registers and 10 blocks); wider points keep about 48 registers.
+// The multi-set packet kernel carries its job loop and set descriptor and
+// gets a little more room; kernels with the per-query traversal keep 64
+// registers (its per-lane stacks).
+constexpr int knn_min_blocks(int dp, bool multi, bool solo)
+{
+    return solo ? 8 : multi ? 8 : (dp <= 4 ? 16 : 10);
+}
 
-// GENERAL = false: one tree, packet traversal only.  GENERAL = true: one tree
-// or many sets, each set's traversal shape chosen by its solo flag.
-template <int DP, bool GENERAL>
-__global__ void __launch_bounds__(kKnnThreads, knn_min_blocks(DP, GENERAL)) k_knn(KnnArgs a)
+// MULTI = false: one tree, warp w takes positions [32 w, 32 w + 32).
+// MULTI = true: many sets; persistent warps take (set, 32 positions) jobs
+// from a device work queue.  SOLO = false: packet traversal only; SOLO =
+// true: each set's shape is chosen by its solo flag.
+template <int DP, bool MULTI, bool SOLO>
+__global__ void __launch_bounds__(kKnnThreads, knn_min_blocks(DP, MULTI, SOLO)) k_knn(KnnArgs a)
 {
     __shared__ __align__(16) float stage_x[kKnnThreads / 32][DP][32];
     __shared__ int stage_id[kKnnThreads / 32][32];
     extern __shared__ unsigned long long heap_mem[];   // [kmax][kKnnThreads]
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     unsigned long long* h = heap_mem + threadIdx.x;
-    if (!GENERAL || !a.jobs) {
+    if (!MULTI) {
         // one tree: warp w takes positions [32 w, 32 w + 32)
         KnnSet S;
         S.nodes = a.nodes;
@@ -462,10 +499,12 @@ __global__ void __launch_bounds__(kKnnThreads, knn_min_blocks(DP, GENERAL)) k_kn
         S.id_base = 0;
         S.row_base = 0;
         S.solo = a.solo;
+        S.nreq = 0;
+        S.reqs = nullptr;
         S.k = a.k;
         const long long g0 = ((long long)blockIdx.x * (kKnnThreads / 32) + warp) * 32;
         if (g0 >= a.m) return;
-        knn_warp_job<DP, GENERAL>(a, S, g0, stage_x[warp], stage_id[warp], h);
+        knn_warp_job<DP, SOLO, false>(a, S, g0, stage_x[warp], stage_id[warp], h);
         return;
     }
     // many sets: persistent warps take jobs from the device work queue
@@ -476,7 +515,7 @@ __global__ void __launch_bounds__(kKnnThreads, knn_min_blocks(DP, GENERAL)) k_kn
         if (j >= a.njobs) break;
         const KnnJob jb = a.jobs[j];
         const KnnSet S = a.sets[jb.set];
-        knn_warp_job<DP, GENERAL>(a, S, jb.pos, stage_x[warp], stage_id[warp], h);
+        knn_warp_job<DP, SOLO, true>(a, S, jb.pos, stage_x[warp], stage_id[warp], h);
         __syncwarp();
     }
 }

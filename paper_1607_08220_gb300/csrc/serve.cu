@@ -124,58 +124,87 @@ struct Server {
 
 namespace {
 
-panda_status enqueue_batch(Server* S, const std::vector<Request*>& batch, InFlight& fl)
+panda_status enqueue_batch(Server* S, const std::vector<Request*>& batch_in, InFlight& fl)
 {
     cudaStream_t s = S->qstream;
-    const int nr = (int)batch.size();
-    const panda_tree* t0 = S->trees[batch[0]->tree];
+    const int nr = (int)batch_in.size();
+    // Requests on the same tree form one query set: their queries are sorted
+    // together by the tree's leaves, so a warp's 32 queries may come from
+    // several requests (each lane finds its own request by batch row).  Rows
+    // are numbered group by group, so each group's sorted positions are one
+    // contiguous range.
+    std::vector<int> group_tree;
+    std::vector<std::vector<const Request*>> groups;
+    for (const Request* R : batch_in) {
+        size_t g = 0;
+        while (g < group_tree.size() && group_tree[g] != R->tree) g++;
+        if (g == group_tree.size()) {
+            group_tree.push_back(R->tree);
+            groups.emplace_back();
+        }
+        groups[g].push_back(R);
+    }
+    const int ng = (int)groups.size();
+    const panda_tree* t0 = S->trees[group_tree[0]];
     const int d = t0->d;
     long long m_total = 0;
     int kmax = 1;
-    std::vector<int> row_begin(nr + 1);
-    std::vector<OrderSet> os(nr);
-    std::vector<KnnSet> ks(nr);
+    std::vector<int> row_begin;
+    std::vector<OrderSet> os;
+    std::vector<KnnReq> kr;
+    std::vector<KnnSet> ks(ng);
+    std::vector<long long> group_begin(ng + 1, 0);
+    std::vector<int> group_req0(ng, 0);
     std::vector<KnnJob> jobs;
     long long bins = 0;
-    for (int r = 0; r < nr; r++) {
-        const Request* R = batch[r];
-        const panda_tree* t = S->trees[R->tree];
-        row_begin[r] = (int)m_total;
-        // bins of this request: about 4 per query, at most 2^20, no finer than a point
-        long long want = std::min<long long>(1LL << 20, std::max<long long>(64, 4 * R->m));
+    int any_solo = 0;
+    for (int g = 0; g < ng; g++) {
+        const panda_tree* t = S->trees[group_tree[g]];
+        long long mg = 0;
+        for (const Request* R : groups[g]) mg += R->m;
+        // bins of this tree: about 4 per query, at most 2^20, no finer than a point
+        const long long want = std::min<long long>(1LL << 20, std::max<long long>(64, 4 * mg));
         int sh = 0;
         while ((t->n >> sh) + 1 > want) sh++;
-        OrderSet& o = os[r];
-        o.nodes = t->nodes;
-        o.num_nodes = t->node_slots;
-        o.queries = R->queries;
-        o.root = 0;
-        o.bin_base = (int)bins;
-        o.shift = sh;
-        o.ns = t->ns;
-        o.row_begin = (int)m_total;
-        o.d = d;
+        group_begin[g] = m_total;
+        group_req0[g] = (int)kr.size();
+        for (const Request* R : groups[g]) {
+            row_begin.push_back((int)m_total);
+            OrderSet o;
+            o.nodes = t->nodes;
+            o.num_nodes = t->node_slots;
+            o.queries = R->queries;
+            o.root = 0;
+            o.bin_base = (int)bins;
+            o.shift = sh;
+            o.ns = t->ns;
+            o.row_begin = (int)m_total;
+            o.d = d;
+            os.push_back(o);
+            kr.push_back(KnnReq{R->queries, R->ids, R->d2, R->k, (int)m_total});
+            m_total += R->m;
+            kmax = std::max(kmax, R->k);
+        }
         bins += (t->n >> sh) + 1;
-        KnnSet& K = ks[r];
+        KnnSet& K = ks[g];
         memset(&K, 0, sizeof(K));
         K.nodes = t->nodes;
         K.pts = t->points;
         K.num_nodes = t->node_slots;
         K.npts = t->n;
-        K.queries = R->queries;
-        K.ids = R->ids;
-        K.d2 = R->d2;
-        K.m = R->m;
+        K.m = mg;
         K.root = 0;
         K.id_base = 0;
-        K.k = R->k;
-        K.row_base = (int)m_total;
-        K.solo = prefer_per_query(R->m, t->n, t->d);
-        for (long long p = 0; p < R->m; p += 32) jobs.push_back(KnnJob{r, (int)p});
-        m_total += R->m;
-        kmax = std::max(kmax, R->k);
+        K.k = kmax;
+        K.row_base = 0;
+        K.solo = prefer_per_query(mg, t->n, t->d);
+        any_solo |= K.solo;
+        K.nreq = (int)groups[g].size();
+        for (long long p = 0; p < mg; p += 32) jobs.push_back(KnnJob{g, (int)p});
     }
-    row_begin[nr] = (int)m_total;
+    group_begin[ng] = m_total;
+    const int nq = (int)kr.size();   // == nr
+    row_begin.push_back((int)m_total);
     const int nb = (int)bins;
     const int nblk = (nb + 4095) / 4096;
     auto get = [&](void** p, size_t bytes, const char* what) -> panda_status {
@@ -188,6 +217,7 @@ panda_status enqueue_batch(Server* S, const std::vector<Request*>& batch, InFlig
     unsigned* err;
     OrderSet* d_os;
     KnnSet* d_ks;
+    KnnReq* d_kr;
     KnnJob* d_jobs;
     panda_status st;
     if ((st = get((void**)&keys, m_total * 4, "served keys")) != PANDA_OK) return st;
@@ -198,13 +228,18 @@ panda_status enqueue_batch(Server* S, const std::vector<Request*>& batch, InFlig
     if ((st = get((void**)&head, 4, "served queue head")) != PANDA_OK) return st;
     if ((st = get((void**)&err, 4, "served error word")) != PANDA_OK) return st;
     if ((st = get((void**)&d_os, nr * sizeof(OrderSet), "served order sets")) != PANDA_OK) return st;
-    if ((st = get((void**)&d_ks, nr * sizeof(KnnSet), "served query sets")) != PANDA_OK) return st;
+    if ((st = get((void**)&d_ks, ng * sizeof(KnnSet), "served query sets")) != PANDA_OK) return st;
+    if ((st = get((void**)&d_kr, nq * sizeof(KnnReq), "served requests")) != PANDA_OK) return st;
     if ((st = get((void**)&d_jobs, std::max<size_t>(jobs.size(), 1) * sizeof(KnnJob), "served jobs")) != PANDA_OK)
         return st;
-    for (int r = 0; r < nr; r++) ks[r].perm = perm + row_begin[r];
+    for (int g = 0; g < ng; g++) {
+        ks[g].perm = perm + group_begin[g];
+        ks[g].reqs = d_kr + group_req0[g];
+    }
     PANDA_CUDA(cudaMemcpyAsync(rb, row_begin.data(), (nr + 1) * 4, cudaMemcpyHostToDevice, s), "served copy");
     PANDA_CUDA(cudaMemcpyAsync(d_os, os.data(), nr * sizeof(OrderSet), cudaMemcpyHostToDevice, s), "served copy");
-    PANDA_CUDA(cudaMemcpyAsync(d_ks, ks.data(), nr * sizeof(KnnSet), cudaMemcpyHostToDevice, s), "served copy");
+    PANDA_CUDA(cudaMemcpyAsync(d_ks, ks.data(), ng * sizeof(KnnSet), cudaMemcpyHostToDevice, s), "served copy");
+    PANDA_CUDA(cudaMemcpyAsync(d_kr, kr.data(), nq * sizeof(KnnReq), cudaMemcpyHostToDevice, s), "served copy");
     if (!jobs.empty())
         PANDA_CUDA(cudaMemcpyAsync(d_jobs, jobs.data(), jobs.size() * sizeof(KnnJob), cudaMemcpyHostToDevice, s),
                    "served copy");
@@ -232,6 +267,7 @@ panda_status enqueue_batch(Server* S, const std::vector<Request*>& batch, InFlig
         ka.d = d;
         ka.k = kmax;
         ka.transpose_max = 12;
+        ka.solo = any_solo;
         switch (t0->dp) {
             case 2: st = launch_knn_dp<2>(ka, s); break;
             case 3: st = launch_knn_dp<3>(ka, s); break;
