@@ -194,9 +194,14 @@ void panda_batch_free(panda_batch* batch);
  * A server keeps trees resident and answers KNN requests asynchronously.  A
  * scheduler thread takes queued requests in arrival order -- any tree, size
  * and k (1..64) -- into batches of at most max_batch_queries queries (a larger
- * request runs alone) and runs each batch as one query-ordering pass and one
- * persistent traversal launch; up to two batches are in flight, so requests
- * arriving while one runs join the next.  Results equal panda_knn's.
+ * request runs alone) and runs each batch as one query-ordering pass (the
+ * queries of all requests on one tree sorted together by its leaves) and one
+ * traversal launch; up to four batches are in flight, each on its own
+ * stream, so requests arriving while batches run join the next one and small
+ * batches overlap.  Results equal panda_knn's.  A
+ * request with a non-finite query coordinate finishes with
+ * PANDA_ERR_NONFINITE_INPUT (its output rows are then unspecified); the other
+ * requests of its batch are unaffected.
  * panda_server_add_tree builds on the server's own stream (queries continue)
  * and is refused with PANDA_ERR_OUT_OF_MEMORY if mem_budget_bytes (0 = no
  * budget) or the device's free memory cannot hold it.  Requests reference

@@ -8,10 +8,10 @@
 
 namespace panda {
 
-template <int DP, bool MULTI, bool SOLO>
+template <int DP, int MODE, bool SOLO>
 panda_status configure_knn_variant()
 {
-    PANDA_CUDA(cudaFuncSetAttribute(k_knn<DP, MULTI, SOLO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    PANDA_CUDA(cudaFuncSetAttribute(k_knn<DP, MODE, SOLO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     kMaxK * kKnnThreads * 8),
                "configure k_knn");
     return PANDA_OK;
@@ -31,7 +31,7 @@ panda_status fill_multi_blocks()
 {
     for (int k = 1; k <= kMaxK; k++) {
         int v = 0;
-        PANDA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_knn<DP, true, SOLO>, kKnnThreads,
+        PANDA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_knn<DP, kKnnManySets, SOLO>, kKnnThreads,
                                                                  (size_t)k * kKnnThreads * 8),
                    "k_knn occupancy");
         multi_blocks_per_sm<DP>()[SOLO ? 1 : 0][k] = v > 0 ? v : 1;
@@ -44,10 +44,12 @@ panda_status configure_knn()
 {
     static bool configured = false;
     if (!configured) {
-        panda_status st = configure_knn_variant<DP, false, false>();
-        if (st == PANDA_OK) st = configure_knn_variant<DP, false, true>();
-        if (st == PANDA_OK) st = configure_knn_variant<DP, true, false>();
-        if (st == PANDA_OK) st = configure_knn_variant<DP, true, true>();
+        panda_status st = configure_knn_variant<DP, kKnnOneSet, false>();
+        if (st == PANDA_OK) st = configure_knn_variant<DP, kKnnOneSet, true>();
+        if (st == PANDA_OK) st = configure_knn_variant<DP, kKnnOneTreeReqs, false>();
+        if (st == PANDA_OK) st = configure_knn_variant<DP, kKnnOneTreeReqs, true>();
+        if (st == PANDA_OK) st = configure_knn_variant<DP, kKnnManySets, false>();
+        if (st == PANDA_OK) st = configure_knn_variant<DP, kKnnManySets, true>();
         if (st == PANDA_OK) st = fill_multi_blocks<DP, false>();
         if (st == PANDA_OK) st = fill_multi_blocks<DP, true>();
         if (st != PANDA_OK) return st;
@@ -62,13 +64,14 @@ panda_status launch_knn_multi(const KnnArgs& a, size_t heap_bytes, cudaStream_t 
 {
     const int per_sm = multi_blocks_per_sm<DP>()[SOLO ? 1 : 0][std::min(std::max(a.k, 1), kMaxK)];
     const long long blocks = (long long)num_sms() * per_sm;
-    k_knn<DP, true, SOLO><<<(unsigned)blocks, kKnnThreads, heap_bytes, s>>>(a);
+    k_knn<DP, kKnnManySets, SOLO><<<(unsigned)blocks, kKnnThreads, heap_bytes, s>>>(a);
     PANDA_LAUNCHED("k_knn");
     return PANDA_OK;
 }
 
-// a.jobs selects the multi-set kernel; a.solo = 1 compiles in the per-query
-// traversal (for a multi-set launch: some set has its solo flag set).
+// a.jobs selects the multi-set kernel, a.reqs the one-tree kernel with the
+// per-lane request lookup; a.solo = 1 compiles in the per-query traversal
+// (for a multi-set launch: some set has its solo flag set).
 template <int DP>
 panda_status launch_knn_dp(const KnnArgs& a, cudaStream_t s)
 {
@@ -83,10 +86,16 @@ panda_status launch_knn_dp(const KnnArgs& a, cudaStream_t s)
     const long long warps = (a.m + 31) / 32;
     const long long blocks = (warps + kKnnThreads / 32 - 1) / (kKnnThreads / 32);
     if (blocks <= 0) return PANDA_OK;
-    if (a.solo)
-        k_knn<DP, false, true><<<(unsigned)blocks, kKnnThreads, heap_bytes, s>>>(a);
-    else
-        k_knn<DP, false, false><<<(unsigned)blocks, kKnnThreads, heap_bytes, s>>>(a);
+    if (a.reqs) {
+        if (a.solo)
+            k_knn<DP, kKnnOneTreeReqs, true><<<(unsigned)blocks, kKnnThreads, heap_bytes, s>>>(a);
+        else
+            k_knn<DP, kKnnOneTreeReqs, false><<<(unsigned)blocks, kKnnThreads, heap_bytes, s>>>(a);
+    } else if (a.solo) {
+        k_knn<DP, kKnnOneSet, true><<<(unsigned)blocks, kKnnThreads, heap_bytes, s>>>(a);
+    } else {
+        k_knn<DP, kKnnOneSet, false><<<(unsigned)blocks, kKnnThreads, heap_bytes, s>>>(a);
+    }
     PANDA_LAUNCHED("k_knn");
     return PANDA_OK;
 }

@@ -39,6 +39,7 @@ struct KnnReq {
     const float* queries;
     int* ids;
     float* d2;
+    unsigned* err;   // the request's own error word (non-finite query)
     int k, row_begin;
 };
 
@@ -87,7 +88,14 @@ struct KnnArgs {
     int d, k;
     int transpose_max;    // use the transposed scan when at most this many lanes need a bucket
     int solo;             // single tree: per-query traversal; many sets: some set has solo set
+    int nreq;             // single tree serving several requests: entries of reqs
+    const KnnReq* reqs;   // (queries / ids / d2 / k above unused; perm lists batch rows)
 };
+
+// Kernel modes: one tree and one query set; one tree and the queries of
+// several requests (per-lane request lookup); many sets from a job queue (a
+// set may span several requests).
+enum KnnMode { kKnnOneSet = 0, kKnnOneTreeReqs = 1, kKnnManySets = 2 };
 
 constexpr unsigned long long kKeyEmpty = (0x7f800000ull << 32) | 0xffffffffull;
 constexpr int kKnnThreads = 128;
@@ -227,9 +235,9 @@ __device__ __forceinline__ void knn_lane_solo(const KnnArgs& a, const KnnSet& S,
 
 // Traversal of one warp job: positions [g0, g0 + 32) of set S.  SOLO_OK
 // compiles the per-query traversal in (taken when S.solo is set); without it
-// the kernel holds the packet traversal alone and keeps its registers.  MULTI
+// the kernel holds the packet traversal alone and keeps its registers.  REQS
 // compiles in the per-lane request lookup of sets that span several requests.
-template <int DP, bool SOLO_OK, bool MULTI>
+template <int DP, bool SOLO_OK, bool REQS>
 __device__ __forceinline__ void knn_warp_job(const KnnArgs& a, const KnnSet& S, long long g0,
                                              float (*sx)[32], int* sid, unsigned long long* h)
 {
@@ -243,8 +251,9 @@ __device__ __forceinline__ void knn_warp_job(const KnnArgs& a, const KnnSet& S, 
     const float* qsrc = S.queries;
     int* out_ids = S.ids;
     float* out_d2 = S.d2;
+    unsigned* qerr = a.err;
     int K = S.k;
-    if (MULTI && S.nreq > 0 && valid) {
+    if (REQS && S.nreq > 0 && valid) {
         // the request holding batch row qi: the last one starting at or before it
         int lo = 0, hi = S.nreq - 1;
         while (lo < hi) {
@@ -255,6 +264,7 @@ __device__ __forceinline__ void knn_warp_job(const KnnArgs& a, const KnnSet& S, 
         qsrc = R.queries;
         out_ids = R.ids;
         out_d2 = R.d2;
+        qerr = R.err;
         K = R.k;
         qi -= R.row_begin;
     }
@@ -265,7 +275,7 @@ __device__ __forceinline__ void knn_warp_job(const KnnArgs& a, const KnnSet& S, 
         q[k] = (valid && k < a.d) ? qsrc[(long long)qi * a.d + k] : 0.0f;
         finite &= (__float_as_uint(q[k]) & 0x7f800000u) != 0x7f800000u;
     }
-    if (!finite) atomicOr(a.err, kErrNonfinite);
+    if (!finite) atomicOr(qerr, kErrNonfinite);
     for (int i = 0; i < K; i++) h[i * kKnnThreads] = kKeyEmpty;
     // k-th best key so far (the heap root); invalid lanes never accept anything
     unsigned long long kth = valid ? kKeyEmpty : 0ull;
@@ -459,31 +469,31 @@ __device__ __forceinline__ void knn_warp_job(const KnnArgs& a, const KnnSet& S, 
 }
 
 
-// Resident blocks per SM the register allocation must allow.  The one-tree
+// Resident blocks per SM the register allocation must allow.  The one-set
 // packet traversal at low dimension fits 32 registers with a few bytes of
 // spill and then runs at full occupancy (measured 8% faster on 3-D self-KNN
 // than at 45 registers and 10 blocks); wider points keep about 48 registers.
-// The multi-set packet kernel carries its job loop and set descriptor and
-// gets a little more room; kernels with the per-query traversal keep 64
-// registers (its per-lane stacks).
-constexpr int knn_min_blocks(int dp, bool multi, bool solo)
+// The request lookup and the job queue hold a few more values; kernels with
+// the per-query traversal keep 64 registers (its per-lane stacks).
+constexpr int knn_min_blocks(int dp, int mode, bool solo)
 {
-    return solo ? 8 : multi ? 8 : (dp <= 4 ? 16 : 10);
+    return solo ? 8 : mode == kKnnManySets ? 8 : mode == kKnnOneTreeReqs ? (dp <= 4 ? 12 : 8)
+                                                                          : (dp <= 4 ? 16 : 10);
 }
 
-// MULTI = false: one tree, warp w takes positions [32 w, 32 w + 32).
-// MULTI = true: many sets; persistent warps take (set, 32 positions) jobs
-// from a device work queue.  SOLO = false: packet traversal only; SOLO =
-// true: each set's shape is chosen by its solo flag.
-template <int DP, bool MULTI, bool SOLO>
-__global__ void __launch_bounds__(kKnnThreads, knn_min_blocks(DP, MULTI, SOLO)) k_knn(KnnArgs a)
+// MODE kKnnOneSet / kKnnOneTreeReqs: one tree, warp w takes positions
+// [32 w, 32 w + 32).  MODE kKnnManySets: persistent warps take (set, 32
+// positions) jobs from a device work queue.  SOLO = false: packet traversal
+// only; SOLO = true: each set's shape is chosen by its solo flag.
+template <int DP, int MODE, bool SOLO>
+__global__ void __launch_bounds__(kKnnThreads, knn_min_blocks(DP, MODE, SOLO)) k_knn(KnnArgs a)
 {
     __shared__ __align__(16) float stage_x[kKnnThreads / 32][DP][32];
     __shared__ int stage_id[kKnnThreads / 32][32];
     extern __shared__ unsigned long long heap_mem[];   // [kmax][kKnnThreads]
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     unsigned long long* h = heap_mem + threadIdx.x;
-    if (!MULTI) {
+    if (MODE != kKnnManySets) {
         // one tree: warp w takes positions [32 w, 32 w + 32)
         KnnSet S;
         S.nodes = a.nodes;
@@ -499,12 +509,12 @@ __global__ void __launch_bounds__(kKnnThreads, knn_min_blocks(DP, MULTI, SOLO)) 
         S.id_base = 0;
         S.row_base = 0;
         S.solo = a.solo;
-        S.nreq = 0;
-        S.reqs = nullptr;
+        S.nreq = MODE == kKnnOneTreeReqs ? a.nreq : 0;
+        S.reqs = a.reqs;
         S.k = a.k;
         const long long g0 = ((long long)blockIdx.x * (kKnnThreads / 32) + warp) * 32;
         if (g0 >= a.m) return;
-        knn_warp_job<DP, SOLO, false>(a, S, g0, stage_x[warp], stage_id[warp], h);
+        knn_warp_job<DP, SOLO, MODE == kKnnOneTreeReqs>(a, S, g0, stage_x[warp], stage_id[warp], h);
         return;
     }
     // many sets: persistent warps take jobs from the device work queue

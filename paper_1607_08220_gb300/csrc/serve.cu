@@ -7,10 +7,12 @@
 // batches from the request queue in arrival order -- requests of different
 // trees, sizes and k -- and runs each batch as one ordering pass (one counting
 // sort over all its queries, each request keyed by the leaves of its own
-// tree) and one persistent traversal launch whose warps take (request, 32
-// queries) jobs from a device work queue.  Up to two batches are in flight:
-// requests that arrive while one runs join the next as soon as a slot frees.
-// Each request records its submit and completion times.
+// tree) and one traversal launch; requests on the same tree are ordered
+// together, so a warp's 32 queries may belong to several requests.  Up to four
+// batches are in flight, each on its own stream (a small batch leaves most of
+// the GPU idle, so batches overlap); requests that arrive while batches run
+// join the next one as soon as a slot frees.  Each request records its submit
+// and completion times.
 #include <string.h>
 
 #include <atomic>
@@ -89,7 +91,8 @@ struct Request {
 
 struct InFlight {
     int64_t batch_id = 0;
-    std::vector<int64_t> reqs;
+    std::vector<int64_t> reqs;   // request ids; entry r owns error word 1 + r of the slot
+    int slot = 0;                // pinned error region of this batch
     cudaEvent_t done = nullptr;
     std::vector<void*> scratch;
 };
@@ -100,8 +103,17 @@ struct Server {
     int device = 0;
     int64_t budget = 0, used = 0;
     int64_t max_batch_queries = 0;
-    int max_inflight = 2;
-    cudaStream_t qstream = nullptr, bstream = nullptr;
+    // Batches in flight at most, each on its own stream: a small batch does
+    // not fill the GPU, so batches run concurrently.
+    static constexpr int kSlots = 4;
+    int max_inflight = kSlots;
+    // Pinned host copies of each in-flight batch's error words: [0] the
+    // batch's (internal errors), [1 + r] request r's (non-finite query).
+    unsigned* h_err[kSlots] = {};
+    int h_err_cap[kSlots] = {};
+    bool slot_busy[kSlots] = {};
+    cudaStream_t qstream[kSlots] = {};
+    cudaStream_t bstream = nullptr;
     std::vector<panda_tree*> trees;
     std::vector<int64_t> tree_bytes;
     std::mutex mu;
@@ -126,13 +138,13 @@ namespace {
 
 panda_status enqueue_batch(Server* S, const std::vector<Request*>& batch_in, InFlight& fl)
 {
-    cudaStream_t s = S->qstream;
+    cudaStream_t s = S->qstream[fl.slot];
     const int nr = (int)batch_in.size();
     // Requests on the same tree form one query set: their queries are sorted
     // together by the tree's leaves, so a warp's 32 queries may come from
     // several requests (each lane finds its own request by batch row).  Rows
     // are numbered group by group, so each group's sorted positions are one
-    // contiguous range.
+    // contiguous range, and each group is one traversal launch.
     std::vector<int> group_tree;
     std::vector<std::vector<const Request*>> groups;
     for (const Request* R : batch_in) {
@@ -145,19 +157,25 @@ panda_status enqueue_batch(Server* S, const std::vector<Request*>& batch_in, InF
         groups[g].push_back(R);
     }
     const int ng = (int)groups.size();
-    const panda_tree* t0 = S->trees[group_tree[0]];
-    const int d = t0->d;
+    fl.reqs.clear();
+    for (int g = 0; g < ng; g++)
+        for (const Request* R : groups[g]) fl.reqs.push_back(R->id);
+    if (S->h_err_cap[fl.slot] < nr + 1) {
+        if (S->h_err[fl.slot]) cudaFreeHost(S->h_err[fl.slot]);
+        S->h_err[fl.slot] = nullptr;
+        S->h_err_cap[fl.slot] = 0;
+        const int cap = std::max(nr + 1, 1024);
+        PANDA_CUDA(cudaHostAlloc((void**)&S->h_err[fl.slot], (size_t)cap * sizeof(unsigned), cudaHostAllocDefault),
+                   "served error words");
+        S->h_err_cap[fl.slot] = cap;
+    }
     long long m_total = 0;
-    int kmax = 1;
     std::vector<int> row_begin;
     std::vector<OrderSet> os;
     std::vector<KnnReq> kr;
-    std::vector<KnnSet> ks(ng);
-    std::vector<long long> group_begin(ng + 1, 0);
-    std::vector<int> group_req0(ng, 0);
-    std::vector<KnnJob> jobs;
+    std::vector<long long> group_begin(ng + 1, 0), group_m(ng, 0);
+    std::vector<int> group_req0(ng, 0), group_kmax(ng, 1);
     long long bins = 0;
-    int any_solo = 0;
     for (int g = 0; g < ng; g++) {
         const panda_tree* t = S->trees[group_tree[g]];
         long long mg = 0;
@@ -167,6 +185,7 @@ panda_status enqueue_batch(Server* S, const std::vector<Request*>& batch_in, InF
         int sh = 0;
         while ((t->n >> sh) + 1 > want) sh++;
         group_begin[g] = m_total;
+        group_m[g] = mg;
         group_req0[g] = (int)kr.size();
         for (const Request* R : groups[g]) {
             row_begin.push_back((int)m_total);
@@ -179,31 +198,15 @@ panda_status enqueue_batch(Server* S, const std::vector<Request*>& batch_in, InF
             o.shift = sh;
             o.ns = t->ns;
             o.row_begin = (int)m_total;
-            o.d = d;
+            o.d = t->d;
             os.push_back(o);
-            kr.push_back(KnnReq{R->queries, R->ids, R->d2, R->k, (int)m_total});
+            kr.push_back(KnnReq{R->queries, R->ids, R->d2, nullptr, R->k, (int)m_total});
             m_total += R->m;
-            kmax = std::max(kmax, R->k);
+            group_kmax[g] = std::max(group_kmax[g], R->k);
         }
         bins += (t->n >> sh) + 1;
-        KnnSet& K = ks[g];
-        memset(&K, 0, sizeof(K));
-        K.nodes = t->nodes;
-        K.pts = t->points;
-        K.num_nodes = t->node_slots;
-        K.npts = t->n;
-        K.m = mg;
-        K.root = 0;
-        K.id_base = 0;
-        K.k = kmax;
-        K.row_base = 0;
-        K.solo = prefer_per_query(mg, t->n, t->d);
-        any_solo |= K.solo;
-        K.nreq = (int)groups[g].size();
-        for (long long p = 0; p < mg; p += 32) jobs.push_back(KnnJob{g, (int)p});
     }
     group_begin[ng] = m_total;
-    const int nq = (int)kr.size();   // == nr
     row_begin.push_back((int)m_total);
     const int nb = (int)bins;
     const int nblk = (nb + 4095) / 4096;
@@ -213,39 +216,25 @@ panda_status enqueue_batch(Server* S, const std::vector<Request*>& batch_in, InF
         return st;
     };
     unsigned* keys;
-    int *perm, *hist, *bsum, *rb, *head;
+    int *perm, *hist, *bsum, *rb;
     unsigned* err;
     OrderSet* d_os;
-    KnnSet* d_ks;
     KnnReq* d_kr;
-    KnnJob* d_jobs;
     panda_status st;
     if ((st = get((void**)&keys, m_total * 4, "served keys")) != PANDA_OK) return st;
     if ((st = get((void**)&perm, m_total * 4, "served permutation")) != PANDA_OK) return st;
     if ((st = get((void**)&hist, (size_t)nblk * 4096 * 4, "served histogram")) != PANDA_OK) return st;
     if ((st = get((void**)&bsum, (size_t)nblk * 4, "served block sums")) != PANDA_OK) return st;
     if ((st = get((void**)&rb, (size_t)(nr + 1) * 4, "served row offsets")) != PANDA_OK) return st;
-    if ((st = get((void**)&head, 4, "served queue head")) != PANDA_OK) return st;
-    if ((st = get((void**)&err, 4, "served error word")) != PANDA_OK) return st;
+    if ((st = get((void**)&err, (size_t)(nr + 1) * 4, "served error words")) != PANDA_OK) return st;
+    for (int r = 0; r < nr; r++) kr[r].err = err + 1 + r;
     if ((st = get((void**)&d_os, nr * sizeof(OrderSet), "served order sets")) != PANDA_OK) return st;
-    if ((st = get((void**)&d_ks, ng * sizeof(KnnSet), "served query sets")) != PANDA_OK) return st;
-    if ((st = get((void**)&d_kr, nq * sizeof(KnnReq), "served requests")) != PANDA_OK) return st;
-    if ((st = get((void**)&d_jobs, std::max<size_t>(jobs.size(), 1) * sizeof(KnnJob), "served jobs")) != PANDA_OK)
-        return st;
-    for (int g = 0; g < ng; g++) {
-        ks[g].perm = perm + group_begin[g];
-        ks[g].reqs = d_kr + group_req0[g];
-    }
+    if ((st = get((void**)&d_kr, nr * sizeof(KnnReq), "served requests")) != PANDA_OK) return st;
     PANDA_CUDA(cudaMemcpyAsync(rb, row_begin.data(), (nr + 1) * 4, cudaMemcpyHostToDevice, s), "served copy");
     PANDA_CUDA(cudaMemcpyAsync(d_os, os.data(), nr * sizeof(OrderSet), cudaMemcpyHostToDevice, s), "served copy");
-    PANDA_CUDA(cudaMemcpyAsync(d_ks, ks.data(), ng * sizeof(KnnSet), cudaMemcpyHostToDevice, s), "served copy");
-    PANDA_CUDA(cudaMemcpyAsync(d_kr, kr.data(), nq * sizeof(KnnReq), cudaMemcpyHostToDevice, s), "served copy");
-    if (!jobs.empty())
-        PANDA_CUDA(cudaMemcpyAsync(d_jobs, jobs.data(), jobs.size() * sizeof(KnnJob), cudaMemcpyHostToDevice, s),
-                   "served copy");
+    PANDA_CUDA(cudaMemcpyAsync(d_kr, kr.data(), nr * sizeof(KnnReq), cudaMemcpyHostToDevice, s), "served copy");
     PANDA_CUDA(cudaMemsetAsync(hist, 0, (size_t)nb * 4, s), "served clear");
-    PANDA_CUDA(cudaMemsetAsync(head, 0, 4, s), "served clear");
-    PANDA_CUDA(cudaMemsetAsync(err, 0, 4, s), "served clear");
+    PANDA_CUDA(cudaMemsetAsync(err, 0, (size_t)(nr + 1) * 4, s), "served clear");
     if (m_total > 0) {
         const unsigned gb = (unsigned)((m_total + 255) / 256);
         k_order_keys_multi<<<gb, 256, 0, s>>>(d_os, rb, nr, m_total, keys, hist);
@@ -256,28 +245,101 @@ panda_status enqueue_batch(Server* S, const std::vector<Request*>& batch_in, InF
         PANDA_LAUNCHED("k_scan_sums");
         k_order_scatter<<<gb, 256, 0, s>>>(keys, m_total, hist, bsum, perm);
         PANDA_LAUNCHED("k_order_scatter");
-        KnnArgs ka;
-        memset(&ka, 0, sizeof(ka));
-        ka.sets = d_ks;
-        ka.jobs = d_jobs;
-        ka.njobs = (int)jobs.size();
-        ka.job_head = head;
-        ka.err = err;
-        ka.m = m_total;
-        ka.d = d;
-        ka.k = kmax;
-        ka.transpose_max = 12;
-        ka.solo = any_solo;
-        switch (t0->dp) {
-            case 2: st = launch_knn_dp<2>(ka, s); break;
-            case 3: st = launch_knn_dp<3>(ka, s); break;
-            case 4: st = launch_knn_dp<4>(ka, s); break;
-            case 8: st = launch_knn_dp<8>(ka, s); break;
-            case 10: st = launch_knn_dp<10>(ka, s); break;
-            default: st = launch_knn_dp<16>(ka, s); break;
+        int any_solo = 0, kmax = 1;
+        for (int g = 0; g < ng; g++) {
+            const panda_tree* t = S->trees[group_tree[g]];
+            any_solo |= prefer_per_query(group_m[g], t->n, t->d);
+            kmax = std::max(kmax, group_kmax[g]);
+        }
+        if (ng > 1 || any_solo) {
+            // several trees, or per-query traversal (lanes of very uneven
+            // work): one persistent launch whose warps take (tree, 32 queries)
+            // jobs from a device queue, so no launch waits on another's tail
+            std::vector<KnnSet> ks(ng);
+            std::vector<KnnJob> jobs;
+            for (int g = 0; g < ng; g++) {
+                const panda_tree* t = S->trees[group_tree[g]];
+                KnnSet& K = ks[g];
+                memset(&K, 0, sizeof(K));
+                K.nodes = t->nodes;
+                K.pts = t->points;
+                K.num_nodes = t->node_slots;
+                K.npts = t->n;
+                K.perm = perm + group_begin[g];
+                K.m = group_m[g];
+                K.k = group_kmax[g];
+                K.solo = prefer_per_query(group_m[g], t->n, t->d);
+                K.nreq = (int)groups[g].size();
+                K.reqs = d_kr + group_req0[g];
+                for (long long p = 0; p < group_m[g]; p += 32) jobs.push_back(KnnJob{g, (int)p});
+            }
+            KnnSet* d_ks;
+            KnnJob* d_jobs;
+            int* head;
+            if ((st = get((void**)&d_ks, ng * sizeof(KnnSet), "served query sets")) != PANDA_OK) return st;
+            if ((st = get((void**)&d_jobs, std::max<size_t>(jobs.size(), 1) * sizeof(KnnJob), "served jobs")) !=
+                PANDA_OK)
+                return st;
+            if ((st = get((void**)&head, 4, "served queue head")) != PANDA_OK) return st;
+            PANDA_CUDA(cudaMemcpyAsync(d_ks, ks.data(), ng * sizeof(KnnSet), cudaMemcpyHostToDevice, s),
+                       "served copy");
+            PANDA_CUDA(cudaMemcpyAsync(d_jobs, jobs.data(), jobs.size() * sizeof(KnnJob), cudaMemcpyHostToDevice,
+                                       s),
+                       "served copy");
+            PANDA_CUDA(cudaMemsetAsync(head, 0, 4, s), "served clear");
+            KnnArgs ka;
+            memset(&ka, 0, sizeof(ka));
+            ka.sets = d_ks;
+            ka.jobs = d_jobs;
+            ka.njobs = (int)jobs.size();
+            ka.job_head = head;
+            ka.err = err;
+            ka.m = m_total;
+            ka.d = S->trees[group_tree[0]]->d;
+            ka.k = kmax;
+            ka.transpose_max = 12;
+            ka.solo = any_solo;
+            switch (S->trees[group_tree[0]]->dp) {
+                case 2: st = launch_knn_dp<2>(ka, s); break;
+                case 3: st = launch_knn_dp<3>(ka, s); break;
+                case 4: st = launch_knn_dp<4>(ka, s); break;
+                case 8: st = launch_knn_dp<8>(ka, s); break;
+                case 10: st = launch_knn_dp<10>(ka, s); break;
+                default: st = launch_knn_dp<16>(ka, s); break;
+            }
+        }
+        for (int g = 0; g < ng && st == PANDA_OK && !(ng > 1 || any_solo); g++) {
+            // one tree, packet traversal: tree fields as kernel parameters
+            if (group_m[g] == 0) continue;
+            const panda_tree* t = S->trees[group_tree[g]];
+            KnnArgs ka;
+            memset(&ka, 0, sizeof(ka));
+            ka.nodes = t->nodes;
+            ka.pts = t->points;
+            ka.num_nodes = t->node_slots;
+            ka.npts = t->n;
+            ka.perm = perm + group_begin[g];
+            ka.err = err;
+            ka.m = group_m[g];
+            ka.d = t->d;
+            ka.k = group_kmax[g];
+            ka.transpose_max = 12;
+            ka.solo = prefer_per_query(group_m[g], t->n, t->d);
+            ka.reqs = d_kr + group_req0[g];
+            ka.nreq = (int)groups[g].size();
+            switch (t->dp) {
+                case 2: st = launch_knn_dp<2>(ka, s); break;
+                case 3: st = launch_knn_dp<3>(ka, s); break;
+                case 4: st = launch_knn_dp<4>(ka, s); break;
+                case 8: st = launch_knn_dp<8>(ka, s); break;
+                case 10: st = launch_knn_dp<10>(ka, s); break;
+                default: st = launch_knn_dp<16>(ka, s); break;
+            }
         }
         if (st != PANDA_OK) return st;
     }
+    PANDA_CUDA(cudaMemcpyAsync(S->h_err[fl.slot], err, (size_t)(nr + 1) * 4, cudaMemcpyDeviceToHost, s),
+               "served error words");
     PANDA_CUDA(cudaEventCreateWithFlags(&fl.done, cudaEventDisableTiming), "served event");
     PANDA_CUDA(cudaEventRecord(fl.done, s), "served event");
     return PANDA_OK;
@@ -285,10 +347,20 @@ panda_status enqueue_batch(Server* S, const std::vector<Request*>& batch_in, InF
 
 void release(Server* S, InFlight& fl)
 {
-    for (void* p : fl.scratch) ws_free(p, S->qstream);
+    for (void* p : fl.scratch) ws_free(p, S->qstream[fl.slot]);
     fl.scratch.clear();
     if (fl.done) cudaEventDestroy(fl.done);
     fl.done = nullptr;
+    S->slot_busy[fl.slot] = false;
+}
+
+// Status of request r of a finished batch from its slot's error words.
+panda_status request_status(const Server* S, const InFlight& fl, size_t r)
+{
+    const volatile unsigned* h = S->h_err[fl.slot];
+    if (h[0] != 0) return PANDA_ERR_CUDA;
+    if (h[1 + r] & kErrNonfinite) return PANDA_ERR_NONFINITE_INPUT;
+    return h[1 + r] ? PANDA_ERR_CUDA : PANDA_OK;
 }
 
 void scheduler(Server* S)
@@ -306,11 +378,10 @@ void scheduler(Server* S)
                 continue;
             }
             const int64_t t = S->now_ns();
-            const panda_status st = q == cudaSuccess ? PANDA_OK : PANDA_ERR_CUDA;
-            for (int64_t id : fl.reqs) {
-                Request& R = S->reqs[id];
+            for (size_t r = 0; r < fl.reqs.size(); r++) {
+                Request& R = S->reqs[fl.reqs[r]];
                 R.t_done = t;
-                R.status = st;
+                R.status = q == cudaSuccess ? request_status(S, fl, r) : PANDA_ERR_CUDA;
                 R.done = true;
             }
             release(S, fl);
@@ -337,6 +408,8 @@ void scheduler(Server* S)
             InFlight fl;
             fl.batch_id = S->next_batch++;
             fl.reqs = ids;
+            while (S->slot_busy[fl.slot]) fl.slot++;   // a slot is free: fewer than kSlots in flight
+            S->slot_busy[fl.slot] = true;
             for (Request* R : batch) R->batch = fl.batch_id;
             lk.unlock();
             const panda_status st = enqueue_batch(S, batch, fl);
@@ -387,17 +460,23 @@ panda_status panda_server_create(int64_t mem_budget_bytes, int64_t max_batch_que
     S->budget = mem_budget_bytes;
     S->max_batch_queries = max_batch_queries;
     S->t0 = Clock::now();
-    cudaError_t e = cudaStreamCreateWithFlags(&S->qstream, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S->bstream, cudaStreamNonBlocking);
+    auto destroy_streams = [S] {
+        for (cudaStream_t& q : S->qstream)
+            if (q) cudaStreamDestroy(q);
+        if (S->bstream) cudaStreamDestroy(S->bstream);
+    };
+    cudaError_t e = cudaStreamCreateWithFlags(&S->bstream, cudaStreamNonBlocking);
+    for (int i = 0; i < Server::kSlots && e == cudaSuccess; i++)
+        e = cudaStreamCreateWithFlags(&S->qstream[i], cudaStreamNonBlocking);
     if (e != cudaSuccess) {
+        destroy_streams();
         delete S;
         return cuda_fail(e, "panda_server_create: streams");
     }
     panda_status st = configure_knn_lo();
     if (st == PANDA_OK) st = configure_knn_hi();
     if (st != PANDA_OK) {
-        cudaStreamDestroy(S->qstream);
-        cudaStreamDestroy(S->bstream);
+        destroy_streams();
         delete S;
         return st;
     }
@@ -506,7 +585,10 @@ panda_status panda_server_poll(panda_server* S, int64_t request_id, int32_t* don
         return PANDA_ERR_INVALID_ARGUMENT;
     }
     *done = it->second.done ? 1 : 0;
-    return it->second.done ? it->second.status : PANDA_OK;
+    const panda_status st = it->second.done ? it->second.status : PANDA_OK;
+    if (st != PANDA_OK)
+        set_error("panda_server_poll: request %lld failed: %s", (long long)request_id, panda_status_string(st));
+    return st;
 }
 
 panda_status panda_server_wait(panda_server* S, int64_t request_id, int64_t timeout_us)
@@ -525,7 +607,10 @@ panda_status panda_server_wait(panda_server* S, int64_t request_id, int64_t time
                   (long long)timeout_us);
         return PANDA_ERR_TIMEOUT;
     }
-    return S->reqs[request_id].status;
+    const panda_status st = S->reqs[request_id].status;
+    if (st != PANDA_OK)
+        set_error("panda_server_wait: request %lld failed: %s", (long long)request_id, panda_status_string(st));
+    return st;
 }
 
 panda_status panda_server_request_info(panda_server* S, int64_t request_id, int64_t* t_submit_ns,
@@ -564,9 +649,12 @@ void panda_server_destroy(panda_server* S)
     }
     S->cv.notify_all();
     if (S->sched.joinable()) S->sched.join();
-    cudaStreamSynchronize(S->qstream);
+    for (cudaStream_t q : S->qstream) cudaStreamSynchronize(q);
     for (panda_tree* t : S->trees) panda_free(t);
-    cudaStreamDestroy(S->qstream);
+    for (int i = 0; i < Server::kSlots; i++) {
+        if (S->h_err[i]) cudaFreeHost(S->h_err[i]);
+        cudaStreamDestroy(S->qstream[i]);
+    }
     cudaStreamDestroy(S->bstream);
     delete S;
 }

@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libpanda.so")
 
 ORDER = {"none": 0, "morton": 1, "leaf": 2}
 TRAVERSAL = {"auto": 0, "packet": 1, "per_query": 2}
+STATUS_TIMEOUT = 6
 STATUS_NAMES = {0: "PANDA_OK", 1: "PANDA_ERR_INVALID_ARGUMENT", 2: "PANDA_ERR_NONFINITE_INPUT",
                 3: "PANDA_ERR_UNSUPPORTED", 4: "PANDA_ERR_OUT_OF_MEMORY", 5: "PANDA_ERR_CUDA",
                 6: "PANDA_ERR_TIMEOUT", 7: "PANDA_ERR_QUEUE_FULL", 8: "PANDA_ERR_DEPTH"}
@@ -361,8 +362,10 @@ class Server:
         return bool(done.value)
 
     def wait(self, rid: int, timeout_s: float = 60.0):
-        _check(load().panda_server_wait(self._h, int(rid), int(timeout_s * 1e6)))
-        self._keep.pop(rid, None)
+        st = load().panda_server_wait(self._h, int(rid), int(timeout_s * 1e6))
+        if st != STATUS_TIMEOUT:          # finished (well or not): its buffers are free
+            self._keep.pop(rid, None)
+        _check(st)
 
     def times(self, rid: int):
         """(submit ns, done ns, batch id) on the server's clock."""

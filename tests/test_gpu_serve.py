@@ -126,3 +126,33 @@ def test_admission_budget_and_errors(P):
     srv.wait(rid, 30)
     assert torch.equal(out[0][:, 0].cpu(), torch.arange(100, dtype=torch.int32))
     srv.close()
+
+
+def test_nonfinite_request_fails_alone(P):
+    """A request holding a NaN query fails with PANDA_ERR_NONFINITE_INPUT; the
+    requests batched with it still return panda_knn's answers."""
+    import torch
+    pts = torch.from_numpy(workloads.cosmology_points(100_000, seed=80, halos=20)).cuda()
+    srv = P.Server()
+    t = srv.add_tree(pts)
+    ref = P.build(pts, 32)
+    todo = []
+    for i in range(12):
+        q = torch.from_numpy(workloads.cosmology_points(3000, seed=900 + i, halos=20)).cuda()
+        if i == 5:
+            q[17, 1] = float("nan")
+        out = (torch.empty((3000, 4), dtype=torch.int32, device="cuda"),
+               torch.empty((3000, 4), dtype=torch.float32, device="cuda"))
+        todo.append((q, out))
+    torch.cuda.synchronize()
+    rids = [srv.submit(t, q, 4, out) for q, out in todo]
+    for i, (rid, (q, out)) in enumerate(zip(rids, todo)):
+        if i == 5:
+            with pytest.raises(P.PandaError) as e:
+                srv.wait(rid, 60)
+            assert e.value.status == 2
+            continue
+        srv.wait(rid, 60)
+        ri, rd = alone(P, ref, q, 4)
+        assert torch.equal(out[0], ri) and torch.equal(out[1].view(torch.int32), rd.view(torch.int32))
+    srv.close()
