@@ -273,10 +273,12 @@ int32_t panda_phase_times(const char** names, float* ms, int32_t* launches, int3
  * out_visits [m][2] int32: per query, the tree nodes whose bound did not
  * exceed its k-th distance when popped, and the bucket points it scanned in
  * those nodes -- the work Algorithm 1 needs for that query, used to state
- * algorithmic FLOPs; out_stats [8] uint64, ADDED to (zero it first): warps,
+ * algorithmic FLOPs; out_stats [12] uint64, ADDED to (zero it first): warps,
  * inner nodes, bucket chunks, chunks scanned with lanes = queries, query
  * broadcasts of the lanes = points scan, insertion rounds, candidates,
- * insertions (per-warp event counts of the traversal kernel). */
+ * insertions, pops no lane needed, and the insertion rounds, candidates and
+ * insertions of the lanes = points scans alone (per-warp event counts of the
+ * packet traversal kernel). */
 panda_status panda_knn_visits(const panda_tree* tree, const float* queries, int64_t m, int32_t k,
                               int32_t* out_ids, float* out_d2, int32_t* out_visits,
                               uint64_t* out_stats, const panda_query_params* params, void* stream);

@@ -50,6 +50,8 @@ panda_status configure_knn()
         if (st == PANDA_OK) st = configure_knn_variant<DP, kKnnOneTreeReqs, true>();
         if (st == PANDA_OK) st = configure_knn_variant<DP, kKnnManySets, false>();
         if (st == PANDA_OK) st = configure_knn_variant<DP, kKnnManySets, true>();
+        if (st == PANDA_OK) st = configure_knn_variant<DP, kKnnStats, false>();
+        if (st == PANDA_OK) st = configure_knn_variant<DP, kKnnStats, true>();
         if (st == PANDA_OK) st = fill_multi_blocks<DP, false>();
         if (st == PANDA_OK) st = fill_multi_blocks<DP, true>();
         if (st != PANDA_OK) return st;
@@ -86,7 +88,12 @@ panda_status launch_knn_dp(const KnnArgs& a, cudaStream_t s)
     const long long warps = (a.m + 31) / 32;
     const long long blocks = (warps + kKnnThreads / 32 - 1) / (kKnnThreads / 32);
     if (blocks <= 0) return PANDA_OK;
-    if (a.reqs) {
+    if (a.stats || a.visits) {
+        if (a.solo)
+            k_knn<DP, kKnnStats, true><<<(unsigned)blocks, kKnnThreads, heap_bytes, s>>>(a);
+        else
+            k_knn<DP, kKnnStats, false><<<(unsigned)blocks, kKnnThreads, heap_bytes, s>>>(a);
+    } else if (a.reqs) {
         if (a.solo)
             k_knn<DP, kKnnOneTreeReqs, true><<<(unsigned)blocks, kKnnThreads, heap_bytes, s>>>(a);
         else

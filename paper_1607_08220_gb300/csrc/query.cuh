@@ -94,8 +94,9 @@ struct KnnArgs {
 
 // Kernel modes: one tree and one query set; one tree and the queries of
 // several requests (per-lane request lookup); many sets from a job queue (a
-// set may span several requests).
-enum KnnMode { kKnnOneSet = 0, kKnnOneTreeReqs = 1, kKnnManySets = 2 };
+// set may span several requests); one tree and one query set with the work
+// counters (visits, stats) compiled in.
+enum KnnMode { kKnnOneSet = 0, kKnnOneTreeReqs = 1, kKnnManySets = 2, kKnnStats = 3 };
 
 constexpr unsigned long long kKeyEmpty = (0x7f800000ull << 32) | 0xffffffffull;
 constexpr int kKnnThreads = 128;
@@ -237,7 +238,7 @@ __device__ __forceinline__ void knn_lane_solo(const KnnArgs& a, const KnnSet& S,
 // compiles the per-query traversal in (taken when S.solo is set); without it
 // the kernel holds the packet traversal alone and keeps its registers.  REQS
 // compiles in the per-lane request lookup of sets that span several requests.
-template <int DP, bool SOLO_OK, bool REQS>
+template <int DP, bool SOLO_OK, bool REQS, bool STATS>
 __device__ __forceinline__ void knn_warp_job(const KnnArgs& a, const KnnSet& S, long long g0,
                                              float (*sx)[32], int* sid, unsigned long long* h)
 {
@@ -283,8 +284,10 @@ __device__ __forceinline__ void knn_warp_job(const KnnArgs& a, const KnnSet& S, 
     int vnodes = 0, vpts = 0;
     // diagnostics: inner nodes, leaf chunks, lanes=queries chunks, transposed
     // broadcasts, insertion-loop rounds, candidates, insertions
-    unsigned st[7] = {0, 0, 0, 0, 0, 0, 0};
-    const bool stats = a.stats != nullptr;
+    // 7: pops no lane needed, 8-10: rounds, candidates, insertions of the
+    // lanes = points scans
+    unsigned st[11] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    const bool stats = STATS && a.stats != nullptr;
     if (SOLO_OK && S.solo) {
         if (valid) knn_lane_solo<DP>(a, S, q, h, K, kth, vnodes, vpts);
     } else {
@@ -320,8 +323,11 @@ __device__ __forceinline__ void knn_warp_job(const KnnArgs& a, const KnnSet& S, 
         const float kd = __uint_as_float((unsigned)(kth >> 32));
         const bool need = valid && !(bnd > kd);
         const unsigned needm = __ballot_sync(kFull, need);
-        if (!needm) continue;
-        vnodes += need;
+        if (!needm) {
+            if (stats) st[7]++;
+            continue;
+        }
+        if (STATS) vnodes += need;
         const int h0 = __float_as_int(f[0]);
         const int h1 = __float_as_int(f[1]);
         const unsigned meta = __float_as_uint(f[3]);
@@ -353,10 +359,11 @@ __device__ __forceinline__ void knn_warp_job(const KnnArgs& a, const KnnSet& S, 
                     sid[lane] = -1;
                 }
                 __syncwarp();
-                if (need) vpts += c;
+                if (STATS && need) vpts += c;
                 unsigned cand = 0;
                 if (stats) st[1]++;
-                if (__popc(needm) > a.transpose_max) {
+                const bool lanes_queries = __popc(needm) > a.transpose_max;
+                if (lanes_queries) {
                     if (stats) st[2]++;
                     // every lane scans all 32 staged points (sentinels beyond c)
 #pragma unroll
@@ -399,8 +406,13 @@ __device__ __forceinline__ void knn_warp_job(const KnnArgs& a, const KnnSet& S, 
                     }
                 }
                 if (stats) {
-                    st[4] += __reduce_max_sync(kFull, (unsigned)__popc(cand));
-                    st[5] += __popc(cand);
+                    const unsigned r = __reduce_max_sync(kFull, (unsigned)__popc(cand));
+                    st[lanes_queries ? 4 : 8] += r;
+                    st[lanes_queries ? 5 : 9] += __popc(cand);
+                    if (!lanes_queries) {
+                        st[4] += r;
+                        st[5] += __popc(cand);
+                    }
                 }
                 // exact insertion of this lane's candidates
                 while (cand) {
@@ -417,7 +429,10 @@ __device__ __forceinline__ void knn_warp_job(const KnnArgs& a, const KnnSet& S, 
                     if (key < kth) {
                         heap_replace_root(h, K, key);
                         kth = h[0];
-                        if (stats) st[6]++;
+                        if (stats) {
+                            st[6]++;
+                            if (!lanes_queries) st[10]++;
+                        }
                     }
                 }
             }
@@ -442,15 +457,17 @@ __device__ __forceinline__ void knn_warp_job(const KnnArgs& a, const KnnSet& S, 
     }   // packet traversal
     __syncwarp();
     if (stats) {
-        // st[0..4] are warp-uniform (counted once per warp); 5, 6 are per lane
+        // st[0..4], 7, 8 are warp-uniform (counted once per warp); 5, 6, 9, 10 per lane
         st[5] = __reduce_add_sync(kFull, st[5]);
         st[6] = __reduce_add_sync(kFull, st[6]);
+        st[9] = __reduce_add_sync(kFull, st[9]);
+        st[10] = __reduce_add_sync(kFull, st[10]);
         if (lane == 0) {
             atomicAdd(&a.stats[0], 1ull);
-            for (int i = 0; i < 7; i++) atomicAdd(&a.stats[1 + i], (unsigned long long)st[i]);
+            for (int i = 0; i < 11; i++) atomicAdd(&a.stats[1 + i], (unsigned long long)st[i]);
         }
     }
-    if (a.visits && valid) {
+    if (STATS && a.visits && valid) {
         a.visits[2LL * qi] = vnodes;
         a.visits[2LL * qi + 1] = vpts;
     }
@@ -477,8 +494,9 @@ __device__ __forceinline__ void knn_warp_job(const KnnArgs& a, const KnnSet& S, 
 // the per-query traversal keep 64 registers (its per-lane stacks).
 constexpr int knn_min_blocks(int dp, int mode, bool solo)
 {
-    return solo ? 8 : mode == kKnnManySets ? 8 : mode == kKnnOneTreeReqs ? (dp <= 4 ? 12 : 8)
-                                                                          : (dp <= 4 ? 16 : 10);
+    return (solo || mode == kKnnManySets || mode == kKnnStats) ? 8
+           : mode == kKnnOneTreeReqs                          ? (dp <= 4 ? 12 : 8)
+                                                              : (dp <= 4 ? 16 : 10);
 }
 
 // MODE kKnnOneSet / kKnnOneTreeReqs: one tree, warp w takes positions
@@ -514,7 +532,8 @@ __global__ void __launch_bounds__(kKnnThreads, knn_min_blocks(DP, MODE, SOLO)) k
         S.k = a.k;
         const long long g0 = ((long long)blockIdx.x * (kKnnThreads / 32) + warp) * 32;
         if (g0 >= a.m) return;
-        knn_warp_job<DP, SOLO, MODE == kKnnOneTreeReqs>(a, S, g0, stage_x[warp], stage_id[warp], h);
+        knn_warp_job<DP, SOLO, MODE == kKnnOneTreeReqs, MODE == kKnnStats>(a, S, g0, stage_x[warp],
+                                                                           stage_id[warp], h);
         return;
     }
     // many sets: persistent warps take jobs from the device work queue
@@ -525,7 +544,7 @@ __global__ void __launch_bounds__(kKnnThreads, knn_min_blocks(DP, MODE, SOLO)) k
         if (j >= a.njobs) break;
         const KnnJob jb = a.jobs[j];
         const KnnSet S = a.sets[jb.set];
-        knn_warp_job<DP, SOLO, true>(a, S, jb.pos, stage_x[warp], stage_id[warp], h);
+        knn_warp_job<DP, SOLO, true, false>(a, S, jb.pos, stage_x[warp], stage_id[warp], h);
         __syncwarp();
     }
 }

@@ -450,14 +450,15 @@ def knn_visits(tree: Tree, queries, k: int, order: str = "leaf", stream=None, tr
     ids = torch.empty((m, k), dtype=torch.int32, device=q.device)
     d2 = torch.empty((m, k), dtype=torch.float32, device=q.device)
     vis = torch.zeros((m, 2), dtype=torch.int32, device=q.device)
-    stats = torch.zeros(8, dtype=torch.int64, device=q.device)
+    stats = torch.zeros(12, dtype=torch.int64, device=q.device)
     prm = QueryParams(ORDER[order], int(transpose_max), 0, 0)
     _check(L.panda_knn_visits(tree.handle, ctypes.c_void_p(q.data_ptr()), m, int(k),
                               ctypes.c_void_p(ids.data_ptr()), ctypes.c_void_p(d2.data_ptr()),
                               ctypes.c_void_p(vis.data_ptr()), ctypes.c_void_p(stats.data_ptr()),
                               ctypes.byref(prm), _stream_ptr(stream)))
     names = ["warps", "inner_nodes", "bucket_chunks", "lanes_query_chunks", "transposed_broadcasts",
-             "insert_rounds", "candidates", "insertions"]
+             "insert_rounds", "candidates", "insertions", "pruned_pops", "transposed_insert_rounds",
+             "transposed_candidates", "transposed_insertions"]
     return ids, d2, vis, dict(zip(names, stats.cpu().tolist()))
 
 
