@@ -12,7 +12,7 @@ template <int DP, int MODE, bool SOLO>
 panda_status configure_knn_variant()
 {
     PANDA_CUDA(cudaFuncSetAttribute(k_knn<DP, MODE, SOLO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    kMaxK * kKnnThreads * 8),
+                                    (kMaxK + 1) * kKnnThreads * 8),
                "configure k_knn");
     return PANDA_OK;
 }
@@ -32,7 +32,7 @@ panda_status fill_multi_blocks()
     for (int k = 1; k <= kMaxK; k++) {
         int v = 0;
         PANDA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_knn<DP, kKnnManySets, SOLO>, kKnnThreads,
-                                                                 (size_t)k * kKnnThreads * 8),
+                                                                 (size_t)(k + 1) * kKnnThreads * 8),
                    "k_knn occupancy");
         multi_blocks_per_sm<DP>()[SOLO ? 1 : 0][k] = v > 0 ? v : 1;
     }
@@ -79,7 +79,7 @@ panda_status launch_knn_dp(const KnnArgs& a, cudaStream_t s)
 {
     panda_status st = configure_knn<DP>();
     if (st != PANDA_OK) return st;
-    const size_t heap_bytes = (size_t)a.k * kKnnThreads * 8;
+    const size_t heap_bytes = (size_t)(a.k + 1) * kKnnThreads * 8;   // heap + sentinel row
     if (a.jobs) {
         if (a.njobs <= 0) return PANDA_OK;
         return a.solo ? launch_knn_multi<DP, true>(a, heap_bytes, s) : launch_knn_multi<DP, false>(a, heap_bytes, s);

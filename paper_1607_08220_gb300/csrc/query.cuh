@@ -102,7 +102,8 @@ constexpr unsigned long long kKeyEmpty = (0x7f800000ull << 32) | 0xffffffffull;
 constexpr int kKnnThreads = 128;
 
 // Replace the root of the lane's max-heap h[0..k) (stride kKnnThreads) by c
-// and sift it down.  Keys are unique, so c never equals a child.
+// and sift it down.  Keys are unique, so c never equals a child.  h[k] must
+// hold 0, which no child exceeds, so a missing right child needs no test.
 __device__ __forceinline__ void heap_replace_root(unsigned long long* h, int k, unsigned long long c)
 {
     int i = 0;
@@ -110,7 +111,7 @@ __device__ __forceinline__ void heap_replace_root(unsigned long long* h, int k, 
         const int l = 2 * i + 1;
         if (l >= k) break;
         const unsigned long long cl = h[l * kKnnThreads];
-        const unsigned long long cr = (l + 1 < k) ? h[(l + 1) * kKnnThreads] : 0ull;
+        const unsigned long long cr = h[(l + 1) * kKnnThreads];
         const bool right = cr > cl;
         const unsigned long long cm = right ? cr : cl;
         if (cm < c) break;
@@ -278,6 +279,7 @@ __device__ __forceinline__ void knn_warp_job(const KnnArgs& a, const KnnSet& S, 
     }
     if (!finite) atomicOr(qerr, kErrNonfinite);
     for (int i = 0; i < K; i++) h[i * kKnnThreads] = kKeyEmpty;
+    h[K * kKnnThreads] = 0ull;   // sentinel below the heap
     // k-th best key so far (the heap root); invalid lanes never accept anything
     unsigned long long kth = valid ? kKeyEmpty : 0ull;
 
@@ -480,7 +482,11 @@ __device__ __forceinline__ void knn_warp_job(const KnnArgs& a, const KnnSet& S, 
             const int id = (int)(unsigned)(top & 0xffffffffull);
             oi[sz - 1] = id < 0 ? id : id - S.id_base;
             od[sz - 1] = __uint_as_float((unsigned)(top >> 32));
-            if (sz > 1) heap_replace_root(h, sz - 1, h[(sz - 1) * kKnnThreads]);
+            if (sz > 1) {
+                const unsigned long long last = h[(sz - 1) * kKnnThreads];
+                h[(sz - 1) * kKnnThreads] = 0ull;   // sentinel of the shrunk heap
+                heap_replace_root(h, sz - 1, last);
+            }
         }
     }
 }
@@ -508,7 +514,7 @@ __global__ void __launch_bounds__(kKnnThreads, knn_min_blocks(DP, MODE, SOLO)) k
 {
     __shared__ __align__(16) float stage_x[kKnnThreads / 32][DP][32];
     __shared__ int stage_id[kKnnThreads / 32][32];
-    extern __shared__ unsigned long long heap_mem[];   // [kmax][kKnnThreads]
+    extern __shared__ unsigned long long heap_mem[];   // [kmax + 1][kKnnThreads]
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     unsigned long long* h = heap_mem + threadIdx.x;
     if (MODE != kKnnManySets) {
