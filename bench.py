@@ -209,6 +209,16 @@ def run_reference(args):
 # ----------------------------------------------------------------------------- GPU arm
 
 
+# DRAM traffic of the packet traversal kernel (k_knn, d = 3, k = 10) per query:
+# dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture on the
+# cosmology self-KNN at n = m = 2^23 (2.273825 GB + 1.572518 GB), scaled to a
+# full launch by the number of queries.  It describes the kernel as committed
+# with profiles/k_knn_cosmology_n8388608.md and must be re-captured (or
+# dropped) whenever that kernel changes.
+KNN_TRAFFIC = {"workload": "cosmology_self", "d": 3, "k": 10, "bytes_per_query": (2.273825e9 + 1.572518e9) / 2 ** 23,
+               "source": "ncu capture at n = m = 2^23, scaled by queries (profiles/k_knn_cosmology_n8388608.md)"}
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -368,8 +378,12 @@ def run_ours(args):
         sms = torch.cuda.get_device_properties(0).multi_processor_count
         peak = sms * 128 * sm_max * 1e6 / 1e12
         achieved = flops / (dom_ms / 1e3) / 1e12
+        traffic = None
+        if args.workload == KNN_TRAFFIC["workload"] and d == KNN_TRAFFIC["d"] and k == KNN_TRAFFIC["k"]:
+            traffic = KNN_TRAFFIC["bytes_per_query"] * m
         roof = {"kernel": kernel_phases[dom], "bound": "alu", "achieved": achieved, "peak": peak,
-                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
+                "traffic_source": KNN_TRAFFIC["source"] if traffic is not None else None,
                 "algorithmic": f"3*d FP32 ops (sub, mul, add) per needed node box and per scanned bucket "
                                f"point: nodes={int(v[0])} points={int(v[1])} per launch",
                 "peak_source": f"{sms} SMs x 128 FP32 lanes x {sm_max:.0f} MHz (derived)",
@@ -394,7 +408,8 @@ def run_ours(args):
         roof = {"kernel": kernel_phases[dom], "bound": "hbm", "achieved": achieved, "peak": peak,
                 "unit": "GB/s", "frac": achieved / peak, "traffic": None, "algorithmic": desc,
                 "peak_source": f"{peak_src} STREAM-style copy", "ms_per_launch": dom_ms / max(dom_launches, 1)}
-    roof["peak_note"] = f"of {peak_src}"
+    roof["peak_note"] = (f"derived: unit counts x the {peak_src} maximum SM clock" if roof["bound"] == "alu"
+                         else f"of {peak_src}")
     t.free()
 
     cpu = None
