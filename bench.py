@@ -2,8 +2,8 @@
 """Benchmark of the kd-tree build + exact KNN hot path on GB300.
 
 One step = build the kd-tree over the workload's points and answer every query
-(all §8(a) stages: transpose, level passes, subtree stage, packing, query
-ordering, traversal).  Default workload: cosmology-like self-KNN, n = 2^24
+(every stage of the path: transpose, level passes, subtree stage, packing,
+query ordering, traversal).  Default workload: cosmology-like self-KNN, n = 2^24
 points in 3-D, queries = the points, k = 10, B = 32.
 
 Prints ONE JSON line (rank 0).  `value` is whole-job queries/s (every query of
@@ -219,6 +219,23 @@ KNN_TRAFFIC = {"workload": "cosmology_self", "d": 3, "k": 10, "bytes_per_query":
                "source": "ncu capture at n = m = 2^23, scaled by queries (profiles/k_knn_cosmology_n8388608.md)"}
 
 
+def max_over_ranks(x: float, world: int, device: str) -> float:
+    """The largest of every rank's x (a timed region's length); x itself on one rank."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, world: int, seconds: float) -> float:
+    """Replicas: every rank processes units_per_rank in the timed region, whose
+    length is the slowest rank's; the job's rate counts every rank's units."""
+    return world * units_per_rank / seconds
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -319,13 +336,9 @@ def run_ours(args):
     el_ms = start.elapsed_time(end)
     build_ms = sum(ev_b[3 * s].elapsed_time(ev_b[3 * s + 1]) for s in range(args.steps)) / args.steps
     query_ms = sum(ev_b[3 * s + 1].elapsed_time(ev_b[3 * s + 2]) for s in range(args.steps)) / args.steps
-    el_max = el_ms
-    if world > 1:
-        tt = torch.tensor([el_ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        el_max = float(tt.item())
+    el_max = max_over_ranks(el_ms, world, "cuda")
     ms_per_step = el_max / args.steps
-    value = world * m * args.steps / (el_max / 1e3)
+    value = whole_job_rate(m * args.steps, world, el_max / 1e3)
 
     # ---- end to end through the host-buffer C-ABI calls
     e2e = None
@@ -351,12 +364,8 @@ def run_ours(args):
         e1.record(stream)
         torch.cuda.synchronize()
         barrier()
-        e_ms = e0.elapsed_time(e1)
-        if world > 1:
-            tt = torch.tensor([e_ms], device="cuda")
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            e_ms = float(tt.item())
-        e2e = {"value": world * m * args.steps / (e_ms / 1e3), "unit": UNIT,
+        e_ms = max_over_ranks(e0.elapsed_time(e1), world, "cuda")
+        e2e = {"value": whole_job_rate(m * args.steps, world, e_ms / 1e3), "unit": UNIT,
                "h2d_bytes_per_step": int(w.points.nbytes + w.queries.nbytes),
                "d2h_bytes_per_step": int(m * k * 8), "ms_per_step": e_ms / args.steps}
 
