@@ -275,7 +275,8 @@ int32_t panda_phase_times(const char** names, float* ms, int32_t* launches, int3
  * those nodes -- the work Algorithm 1 needs for that query, used to state
  * algorithmic FLOPs; out_stats [12] uint64, ADDED to (zero it first): warps,
  * inner nodes, bucket chunks, chunks scanned with lanes = queries, query
- * broadcasts of the lanes = points scan, insertion rounds, candidates,
+ * broadcasts of the lanes = points scan, insertion rounds (lanes = points
+ * scans; the lanes = queries scan inserts as it goes), candidates,
  * insertions, pops no lane needed, and the insertion rounds, candidates and
  * insertions of the lanes = points scans alone (per-warp event counts of the
  * packet traversal kernel). */

