@@ -739,7 +739,6 @@ __global__ void k_partition(BuildArgs a, int L)
 
 struct WarpMem {
     float* sx;            // [d][TS] coordinates (TS = T + 4: room for the 16-byte alignment offset)
-    int* sid;             // [TS] ids
     unsigned short* ix[2];  // [T] local indices, ping-pong
     int* rh;              // [256] radix histogram
     float* box;           // [2][kMaxDim] lo, hi
@@ -750,7 +749,7 @@ struct WarpMem {
 __host__ __device__ __forceinline__ size_t warp_bytes(int d, int T)
 {
     const size_t TS = (size_t)T + 4;
-    size_t b = 4 * d * TS + 4 * TS + 2 * 2 * (size_t)T + 256 * 4 + 3 * kMaxDim * 4;
+    size_t b = 4 * d * TS + 2 * 2 * (size_t)T + 256 * 4 + 3 * kMaxDim * 4;
     b = (b + 15) & ~(size_t)15;
     return b + (kMaxDepth + 4) * sizeof(int4);
 }
@@ -805,8 +804,7 @@ __global__ void k_subtree(BuildArgs a, int wbytes)
     unsigned char* base = smem + (size_t)warp * wbytes;
     WarpMem w;
     w.sx = reinterpret_cast<float*>(base);
-    w.sid = reinterpret_cast<int*>(w.sx + (size_t)d * TS);
-    w.ix[0] = reinterpret_cast<unsigned short*>(w.sid + TS);
+    w.ix[0] = reinterpret_cast<unsigned short*>(w.sx + (size_t)d * TS);
     w.ix[1] = w.ix[0] + T;
     w.rh = reinterpret_cast<int*>(w.ix[1] + T);
     w.box = reinterpret_cast<float*>(w.rh + 256);
@@ -842,13 +840,13 @@ __global__ void k_subtree(BuildArgs a, int wbytes)
                 float* dst = w.sx + (size_t)k * TS;
                 for (int c = lane; c < nch; c += 32) cp_async16(dst + 4 * c, src + 4 * c);
             }
-            const int* Is = a.ID[par] + g0;
-            for (int c = lane; c < nch; c += 32) cp_async16(w.sid + 4 * c, Is + 4 * c);
             for (int i = lane; i < count; i += 32) w.ix[0][i] = (unsigned short)i;
             cp_async_wait_all();
         }
         const float* sxo = w.sx + off;
-        const int* sido = w.sid + off;
+        // ids stay in global memory (read once, when a leaf is written): the
+        // shared memory they would take is another warp's worth at d = 3
+        const int* gid = a.ID[par] + start;
         int sp = 0;
         if (lane == 0) w.stk[0] = make_int4(0, count, sn.node, sn.depth_parity >> 1);
         sp = 1;
@@ -904,7 +902,7 @@ __global__ void k_subtree(BuildArgs a, int wbytes)
                             int slot = 4 * v4 + q;
                             float val = 0.0f;
                             if (slot < d) val = sxo[(size_t)slot * TS + p];
-                            else if (slot == a.dp) val = __int_as_float(sido[p]);
+                            else if (slot == a.dp) val = __int_as_float(__ldg(gid + p));
                             f[q] = val;
                         }
                         o[v4] = make_float4(f[0], f[1], f[2], f[3]);
