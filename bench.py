@@ -51,6 +51,9 @@ def parse():
                     help="served: replay the stream at these multiples of its arrival rate")
     ap.add_argument("--slo-ms", type=float, default=100.0, help="served: p99 latency target of the sweep")
     ap.add_argument("--order", choices=["leaf", "morton", "none"], default="leaf")
+    ap.add_argument("--query-path", choices=["auto", "self", "general"], default="auto",
+                    help="self: all-points query (panda_knn_self) when the queries are the points; "
+                         "general: panda_knn with the query buffer; auto: self when it applies")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--n", type=int, default=0, help="override n of cosmology_self (profiling runs)")
@@ -209,13 +212,14 @@ def run_reference(args):
 # ----------------------------------------------------------------------------- GPU arm
 
 
-# DRAM traffic of the packet traversal kernel (k_knn, d = 3, k = 10) per query:
-# dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture on the
-# cosmology self-KNN at n = m = 2^23 (2.273825 GB + 1.572518 GB), scaled to a
-# full launch by the number of queries.  It describes the kernel as committed
-# with profiles/k_knn_cosmology_n8388608.md and must be re-captured (or
-# dropped) whenever that kernel changes.
-KNN_TRAFFIC = {"workload": "cosmology_self", "d": 3, "k": 10, "bytes_per_query": (2.273825e9 + 1.572518e9) / 2 ** 23,
+# DRAM traffic of the packet traversal kernel (k_knn, d = 3, k = 10, all-points
+# query) per query: dram__bytes_read.sum + dram__bytes_write.sum of one ncu
+# capture on the cosmology self-KNN at n = m = 2^23 (1.184872 GB + 1.496198 GB),
+# scaled to a full launch by the number of queries.  It describes the kernel as
+# committed with profiles/k_knn_cosmology_n8388608.md and must be re-captured
+# (or dropped) whenever that kernel changes.
+KNN_TRAFFIC = {"workload": "cosmology_self", "path": "self", "d": 3, "k": 10,
+               "bytes_per_query": (1.184872e9 + 1.496198e9) / 2 ** 23,
                "source": "ncu capture at n = m = 2^23, scaled by queries (profiles/k_knn_cosmology_n8388608.md)"}
 
 
@@ -290,9 +294,19 @@ def run_ours(args):
     d2 = torch.empty((m, k), dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
 
+    use_self = self_q and args.query_path != "general"
+    if args.query_path == "self" and not self_q:
+        raise SystemExit("--query-path self needs a workload whose queries are its points")
+
+    def query(t):
+        if use_self:
+            P.knn_self(t, k, out=(ids, d2))
+        else:
+            P.knn(t, q_dev, k, order=args.order, out=(ids, d2))
+
     def step():
         t = P.build(pts_dev, B)
-        P.knn(t, q_dev, k, order=args.order, out=(ids, d2))
+        query(t)
         t.free()
 
     for _ in range(max(3, args.warmup)):
@@ -323,7 +337,7 @@ def run_ours(args):
         t = P.build(pts_dev, B)
         add_phases()
         ev_b[3 * s + 1].record(stream)
-        P.knn(t, q_dev, k, order=args.order, out=(ids, d2))
+        query(t)
         add_phases()
         ev_b[3 * s + 2].record(stream)
         t.free()
@@ -340,6 +354,29 @@ def run_ours(args):
     ms_per_step = el_max / args.steps
     value = whole_job_rate(m * args.steps, world, el_max / 1e3)
 
+    # ---- the general query path on the same workload (query buffer, ordering
+    # pass), for comparison with the all-points path timed above
+    general = None
+    if use_self:
+        def gstep():
+            t = P.build(pts_dev, B)
+            P.knn(t, q_dev, k, order=args.order, out=(ids, d2))
+            t.free()
+        gstep()
+        torch.cuda.synchronize()
+        barrier()
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        for _ in range(args.steps):
+            gstep()
+        g1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        g_ms = max_over_ranks(g0.elapsed_time(g1), world, "cuda")
+        general = {"value": whole_job_rate(m * args.steps, world, g_ms / 1e3), "unit": UNIT,
+                   "ms_per_step": g_ms / args.steps,
+                   "path": "panda_knn with the query buffer (leaf ordering pass + traversal)"}
+
     # ---- end to end through the host-buffer C-ABI calls
     e2e = None
     if not args.no_e2e:
@@ -351,7 +388,10 @@ def run_ours(args):
 
         def step_e2e():
             t = P.build_host(pn, B)
-            P.knn_host(t, qn, k, order=args.order, out=on)
+            if use_self:
+                P.knn_self_host(t, k, out=on)
+            else:
+                P.knn_host(t, qn, k, order=args.order, out=on)
             t.free()
 
         step_e2e()
@@ -366,7 +406,7 @@ def run_ours(args):
         barrier()
         e_ms = max_over_ranks(e0.elapsed_time(e1), world, "cuda")
         e2e = {"value": whole_job_rate(m * args.steps, world, e_ms / 1e3), "unit": UNIT,
-               "h2d_bytes_per_step": int(w.points.nbytes + w.queries.nbytes),
+               "h2d_bytes_per_step": int(w.points.nbytes + (0 if use_self else w.queries.nbytes)),
                "d2h_bytes_per_step": int(m * k * 8), "ms_per_step": e_ms / args.steps}
 
     # ---- roofline of the dominant kernel (outside the timed region: work counts)
@@ -380,7 +420,7 @@ def run_ours(args):
     dom_ms, dom_launches = per_step[dom]
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     if dom == "query.traverse":
-        _, _, vis, kstats = P.knn_visits(t, q_dev, k, order=args.order)
+        _, _, vis, kstats = P.knn_visits(t, None if use_self else q_dev, k, order=args.order)
         torch.cuda.synchronize()
         v = vis.to(torch.int64).sum(dim=0).cpu().numpy()
         flops = 3.0 * d * float(v[0] + v[1])
@@ -388,7 +428,8 @@ def run_ours(args):
         peak = sms * 128 * sm_max * 1e6 / 1e12
         achieved = flops / (dom_ms / 1e3) / 1e12
         traffic = None
-        if args.workload == KNN_TRAFFIC["workload"] and d == KNN_TRAFFIC["d"] and k == KNN_TRAFFIC["k"]:
+        if (args.workload == KNN_TRAFFIC["workload"] and use_self and d == KNN_TRAFFIC["d"]
+                and k == KNN_TRAFFIC["k"]):
             traffic = KNN_TRAFFIC["bytes_per_query"] * m
         roof = {"kernel": kernel_phases[dom], "bound": "alu", "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
@@ -428,7 +469,10 @@ def run_ours(args):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": max(3, args.warmup), "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": workload_config(w, args.order), "clocks": clk, "e2e": e2e, "gpu_launches": launches,
+            "config": dict(workload_config(w, args.order),
+                           query_path="panda_knn_self (all-points query: the tree's packed points in leaf "
+                                      "order are the queries)" if use_self else "panda_knn (query buffer)"),
+            "clocks": clk, "e2e": e2e, "gpu_launches": launches, "general_query_path": general,
             "roofline": roof, "cpu_baseline": cpu,
             "build_pts_per_s": world * n / (build_ms / 1e3), "query_per_s": world * m / (query_ms / 1e3),
             "build_ms": build_ms, "query_ms": query_ms,

@@ -137,6 +137,23 @@ panda_status panda_knn_host(const panda_tree* tree, const float* queries, int64_
                             int32_t* out_ids, float* out_d2, const panda_query_params* params,
                             void* stream);
 
+/* All-points query (the self-KNN of the paper's particle workloads): every
+ * point of the tree is a query, so no query buffer is read -- the queries are
+ * the tree's own packed points, taken in leaf order, which also makes the
+ * query ordering pass unnecessary.  Row i of out_ids / out_d2 (device,
+ * [n][k]) holds the neighbours of input point i, exactly what panda_knn gives
+ * with queries = the points the tree was built from (a point is its own
+ * rank-0 neighbour unless an exact duplicate has a smaller id).  params:
+ * order is ignored, traversal PER_QUERY is honoured (AUTO means packet),
+ * transpose_max as for panda_knn_async.  panda_knn_self blocks until the
+ * results are written; _async only enqueues; _host writes host outputs and
+ * returns after they are on the host. */
+panda_status panda_knn_self(const panda_tree* tree, int32_t k, int32_t* out_ids, float* out_d2);
+panda_status panda_knn_self_async(const panda_tree* tree, int32_t k, int32_t* out_ids, float* out_d2,
+                                  const panda_query_params* params, void* stream);
+panda_status panda_knn_self_host(const panda_tree* tree, int32_t k, int32_t* out_ids, float* out_d2,
+                                 const panda_query_params* params, void* stream);
+
 /* Same query as panda_knn_async (default parameters) for callers that cannot
  * allocate device memory while they query.  No counterpart in the paper: the
  * query ordering's scratch space is a fixed file-scope device array (12.6 MB,
@@ -269,7 +286,8 @@ panda_status panda_tree_copy(const panda_tree* tree, float* host_nodes, float* h
  * that finished on this thread and returns how many there were. */
 void panda_set_phase_timing(int32_t enable);
 int32_t panda_phase_times(const char** names, float* ms, int32_t* launches, int32_t cap);
-/* Same as panda_knn_async, and also writes (each optional, device memory):
+/* Same as panda_knn_async (queries NULL and m = the tree's n: the all-points
+ * query of panda_knn_self_async), and also writes (each optional, device memory):
  * out_visits [m][2] int32: per query, the tree nodes whose bound did not
  * exceed its k-th distance when popped, and the bucket points it scanned in
  * those nodes -- the work Algorithm 1 needs for that query, used to state

@@ -304,6 +304,76 @@ panda_status panda_knn(const panda_tree* tree, const float* queries, int64_t m, 
     return s;
 }
 
+panda_status panda_knn_self_async(const panda_tree* tree, int32_t k, int32_t* out_ids, float* out_d2,
+                                  const panda_query_params* params, void* stream)
+{
+    clear_error();
+    try {
+        return knn_self(tree, k, out_ids, out_d2, params, (cudaStream_t)stream, nullptr);
+    } catch (...) {
+        set_error("panda_knn_self: host exception");
+        return PANDA_ERR_OUT_OF_MEMORY;
+    }
+}
+
+panda_status panda_knn_self(const panda_tree* tree, int32_t k, int32_t* out_ids, float* out_d2)
+{
+    clear_error();
+    unsigned herr = 0;
+    panda_status s;
+    try {
+        s = knn_self(tree, k, out_ids, out_d2, nullptr, nullptr, &herr);
+    } catch (...) {
+        set_error("panda_knn_self: host exception");
+        return PANDA_ERR_OUT_OF_MEMORY;
+    }
+    if (s == PANDA_OK && herr) {
+        set_error("panda_knn_self: internal consistency check failed (0x%x)", herr);
+        return PANDA_ERR_CUDA;
+    }
+    return s;
+}
+
+panda_status panda_knn_self_host(const panda_tree* tree, int32_t k, int32_t* out_ids, float* out_d2,
+                                 const panda_query_params* params, void* stream)
+{
+    clear_error();
+    if (!tree || k < 1 || !out_ids || !out_d2) {
+        set_error("panda_knn_self_host: invalid argument");
+        return PANDA_ERR_INVALID_ARGUMENT;
+    }
+    if (k > kMaxK) {
+        set_error("panda_knn_self_host: k=%d above the maximum %d", k, kMaxK);
+        return PANDA_ERR_UNSUPPORTED;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    void *di = nullptr, *dd = nullptr;
+    const size_t ob = (size_t)tree->n * k * 4;
+    panda_status st = ws_alloc(&di, ob, s, "id staging");
+    if (st == PANDA_OK) st = ws_alloc(&dd, ob, s, "distance staging");
+    unsigned herr = 0;
+    if (st == PANDA_OK) {
+        try {
+            st = knn_self(tree, k, static_cast<int32_t*>(di), static_cast<float*>(dd), params, s, &herr);
+        } catch (...) {
+            st = PANDA_ERR_OUT_OF_MEMORY;
+        }
+    }
+    if (st == PANDA_OK) {
+        cudaError_t e = cudaMemcpyAsync(out_ids, di, ob, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(out_d2, dd, ob, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) st = cuda_fail(e, "panda_knn_self_host copy out");
+    }
+    ws_free(di, s);
+    ws_free(dd, s);
+    if (st == PANDA_OK && herr) {
+        set_error("panda_knn_self_host: internal consistency check failed (0x%x)", herr);
+        return PANDA_ERR_CUDA;
+    }
+    return st;
+}
+
 panda_status panda_knn_host(const panda_tree* tree, const float* queries, int64_t m, int32_t k, int32_t* out_ids,
                             float* out_d2, const panda_query_params* params, void* stream)
 {
@@ -363,6 +433,14 @@ panda_status panda_knn_visits(const panda_tree* tree, const float* queries, int6
         return PANDA_ERR_INVALID_ARGUMENT;
     }
     try {
+        if (!queries) {   // the all-points query of panda_knn_self
+            if (!tree || m != tree->n) {
+                set_error("panda_knn_visits: queries NULL needs m = the tree's n");
+                return PANDA_ERR_INVALID_ARGUMENT;
+            }
+            return knn_self(tree, k, out_ids, out_d2, params, (cudaStream_t)stream, nullptr, out_visits,
+                            reinterpret_cast<unsigned long long*>(out_stats));
+        }
         return knn_query(tree, queries, m, k, out_ids, out_d2, params, (cudaStream_t)stream, nullptr,
                          out_visits, reinterpret_cast<unsigned long long*>(out_stats));
     } catch (...) {

@@ -291,4 +291,60 @@ panda_status knn_query(const panda_tree* t, const float* queries, int64_t m, int
     return PANDA_OK;
 }
 
+panda_status knn_self(const panda_tree* t, int32_t k, int32_t* ids, float* d2, const panda_query_params* params,
+                      cudaStream_t stream, unsigned* host_err, int32_t* visits, unsigned long long* stats)
+{
+    if (host_err) *host_err = 0;
+    if (!t || k < 1 || !ids || !d2) {
+        set_error("panda_knn_self: invalid argument");
+        return PANDA_ERR_INVALID_ARGUMENT;
+    }
+    if (k > kMaxK) {
+        set_error("panda_knn_self: k=%d above the maximum %d", k, kMaxK);
+        return PANDA_ERR_UNSUPPORTED;
+    }
+    if (!is_device_ptr(ids) || !is_device_ptr(d2)) {
+        set_error("panda_knn_self: outputs must be device pointers");
+        return PANDA_ERR_INVALID_ARGUMENT;
+    }
+    PhaseTimer timer(stream);
+    void* errp = nullptr;
+    panda_status st = ws_alloc(&errp, sizeof(unsigned), stream, "query error word");
+    if (st != PANDA_OK) return st;
+    unsigned* err = static_cast<unsigned*>(errp);
+    cudaError_t ce = cudaMemsetAsync(err, 0, sizeof(unsigned), stream);
+    if (ce != cudaSuccess) {
+        ws_free(errp, stream);
+        return cuda_fail(ce, "clear query error");
+    }
+    timer.begin("query.traverse");
+    KnnArgs ka;
+    memset(&ka, 0, sizeof(ka));
+    ka.nodes = t->nodes;
+    ka.pts = t->points;
+    ka.ids = ids;
+    ka.d2 = d2;
+    ka.err = err;
+    ka.m = t->n;
+    ka.num_nodes = t->node_slots;
+    ka.npts = t->n;
+    ka.self_q = 1;
+    ka.visits = visits;
+    ka.stats = stats;
+    ka.transpose_max = (params && params->transpose_max != 0) ? params->transpose_max : 12;
+    ka.solo = (params && params->traversal == PANDA_TRAVERSAL_PER_QUERY) ? 1 : 0;
+    ka.d = t->d;
+    ka.k = k;
+    st = launch_knn(ka, t->dp, stream);
+    timer.end();
+    if (st == PANDA_OK && host_err) {
+        ce = cudaMemcpyAsync(host_err, err, sizeof(unsigned), cudaMemcpyDeviceToHost, stream);
+        if (ce == cudaSuccess) ce = cudaStreamSynchronize(stream);
+        if (ce != cudaSuccess) st = cuda_fail(ce, "query");
+    }
+    ws_free(errp, stream);
+    if (st == PANDA_OK) timer.finish();
+    return st;
+}
+
 }  // namespace panda

@@ -93,6 +93,8 @@ struct KnnArgs {
     int solo;             // single tree: per-query traversal; many sets: some set has solo set
     int nreq;             // single tree serving several requests: entries of reqs
     const KnnReq* reqs;   // (queries / ids / d2 / k above unused; perm lists batch rows)
+    int self_q;           // single tree: the queries are the tree's own points, taken in
+                          // leaf order from the packed records (queries, perm unused)
 };
 
 // Kernel modes: one tree and one query set; one tree and the queries of
@@ -275,10 +277,24 @@ __device__ __forceinline__ void knn_warp_job(const KnnArgs& a, const KnnSet& S, 
     }
     float q[DP];
     bool finite = true;
+    if (!REQS && a.self_q) {
+        // all-points query: position pos is the packed point pos (coordinates,
+        // zero padding, then its id), already finite and in leaf order
+        if (valid) {
+            const float* pp = reinterpret_cast<const float*>(S.pts + pos * NV);
 #pragma unroll
-    for (int k = 0; k < DP; k++) {
-        q[k] = (valid && k < a.d) ? qsrc[(long long)qi * a.d + k] : 0.0f;
-        finite &= (__float_as_uint(q[k]) & 0x7f800000u) != 0x7f800000u;
+            for (int k = 0; k < DP; k++) q[k] = pp[k];
+            qi = __float_as_int(pp[DP]) - S.id_base;
+        } else {
+#pragma unroll
+            for (int k = 0; k < DP; k++) q[k] = 0.0f;
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < DP; k++) {
+            q[k] = (valid && k < a.d) ? qsrc[(long long)qi * a.d + k] : 0.0f;
+            finite &= (__float_as_uint(q[k]) & 0x7f800000u) != 0x7f800000u;
+        }
     }
     if (!finite) atomicOr(qerr, kErrNonfinite);
     for (int i = 0; i < K; i++) h[i * kKnnThreads] = kKeyEmpty;

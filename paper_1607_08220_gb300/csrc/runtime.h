@@ -88,6 +88,10 @@ panda_status knn_query(const panda_tree* t, const float* queries, int64_t m, int
                        int32_t* ids, float* d2, const panda_query_params* params,
                        cudaStream_t stream, unsigned* host_err, int32_t* visits = nullptr,
                        unsigned long long* stats = nullptr);
+// All-points query: every point of the tree as a query, output row = its id.
+panda_status knn_self(const panda_tree* t, int32_t k, int32_t* ids, float* d2, const panda_query_params* params,
+                      cudaStream_t stream, unsigned* host_err, int32_t* visits = nullptr,
+                      unsigned long long* stats = nullptr);
 
 // Forests of independent trees (batched form), in build.cu.
 struct BuildState;

@@ -32,6 +32,9 @@ SIGNATURES = {
     "panda_knn": ([_P, _P, _I64, _I32, _P, _P], ctypes.c_int),
     "panda_knn_async": ([_P, _P, _I64, _I32, _P, _P, _P, _P], ctypes.c_int),
     "panda_knn_host": ([_P, _P, _I64, _I32, _P, _P, _P, _P], ctypes.c_int),
+    "panda_knn_self": ([_P, _I32, _P, _P], ctypes.c_int),
+    "panda_knn_self_async": ([_P, _I32, _P, _P, _P, _P], ctypes.c_int),
+    "panda_knn_self_host": ([_P, _I32, _P, _P, _P, _P], ctypes.c_int),
     "panda_knn_visits": ([_P, _P, _I64, _I32, _P, _P, _P, _P, _P, _P], ctypes.c_int),
     "panda_knn_noalloc": ([_P, _P, _I64, _I32, _P, _P, _P], ctypes.c_int),
     "panda_batch_create": ([_P, _I32, _I32, _I32, ctypes.POINTER(_P)], ctypes.c_int),
@@ -440,19 +443,67 @@ def knn(tree: Tree, queries, k: int, order: str = "leaf", stream=None, out=None,
     return ids, d2
 
 
-def knn_visits(tree: Tree, queries, k: int, order: str = "leaf", stream=None, transpose_max: int = 0):
-    """KNN plus per-query work counts [m][2] (nodes needed, bucket points scanned)
-    and the traversal's event counters (dict)."""
+def knn_self(tree: Tree, k: int, stream=None, out=None, transpose_max: int = 0, traversal: str = "auto"):
+    """All-points KNN: every point of the tree is a query (row i = input point i).
+
+    Enqueued on `stream`; returns (ids int32 [n][k], d2 float32 [n][k]) CUDA tensors."""
     torch = _torch()
     L = load()
-    q = _as_device_points(queries, "queries")
-    m = q.shape[0]
-    ids = torch.empty((m, k), dtype=torch.int32, device=q.device)
-    d2 = torch.empty((m, k), dtype=torch.float32, device=q.device)
-    vis = torch.zeros((m, 2), dtype=torch.int32, device=q.device)
-    stats = torch.zeros(12, dtype=torch.int64, device=q.device)
+    n = tree.info()["n"]
+    if out is None:
+        ids = torch.empty((n, k), dtype=torch.int32, device="cuda")
+        d2 = torch.empty((n, k), dtype=torch.float32, device="cuda")
+    else:
+        ids, d2 = out
+    prm = QueryParams(ORDER["leaf"], int(transpose_max), TRAVERSAL[traversal], 0)
+    _check(L.panda_knn_self_async(tree.handle, int(k), ctypes.c_void_p(ids.data_ptr()),
+                                  ctypes.c_void_p(d2.data_ptr()), ctypes.byref(prm), _stream_ptr(stream)))
+    return ids, d2
+
+
+def knn_self_sync(tree: Tree, k: int):
+    """panda_knn_self: blocking all-points query on the legacy stream."""
+    torch = _torch()
+    L = load()
+    n = tree.info()["n"]
+    ids = torch.empty((n, k), dtype=torch.int32, device="cuda")
+    d2 = torch.empty((n, k), dtype=torch.float32, device="cuda")
+    torch.cuda.current_stream().synchronize()
+    _check(L.panda_knn_self(tree.handle, int(k), ctypes.c_void_p(ids.data_ptr()), ctypes.c_void_p(d2.data_ptr())))
+    return ids, d2
+
+
+def knn_self_host(tree: Tree, k: int, stream=None, out: tuple | None = None):
+    """panda_knn_self_host: all-points query into host outputs (copy out inside the call)."""
+    L = load()
+    n = tree.info()["n"]
+    if out is None:
+        ids = np.empty((n, k), np.int32)
+        d2 = np.empty((n, k), np.float32)
+    else:
+        ids, d2 = out
+    prm = QueryParams(ORDER["leaf"], 0, 0, 0)
+    _check(L.panda_knn_self_host(tree.handle, int(k), ids.ctypes.data_as(ctypes.c_void_p),
+                                 d2.ctypes.data_as(ctypes.c_void_p), ctypes.byref(prm), _stream_ptr(stream)))
+    return ids, d2
+
+
+def knn_visits(tree: Tree, queries, k: int, order: str = "leaf", stream=None, transpose_max: int = 0):
+    """KNN plus per-query work counts [m][2] (nodes needed, bucket points scanned)
+    and the traversal's event counters (dict).  queries=None: the all-points query."""
+    torch = _torch()
+    L = load()
+    if queries is None:
+        q, m, qp = None, tree.info()["n"], None
+    else:
+        q = _as_device_points(queries, "queries")
+        m, qp = q.shape[0], q.data_ptr()
+    ids = torch.empty((m, k), dtype=torch.int32, device="cuda")
+    d2 = torch.empty((m, k), dtype=torch.float32, device="cuda")
+    vis = torch.zeros((m, 2), dtype=torch.int32, device="cuda")
+    stats = torch.zeros(12, dtype=torch.int64, device="cuda")
     prm = QueryParams(ORDER[order], int(transpose_max), 0, 0)
-    _check(L.panda_knn_visits(tree.handle, ctypes.c_void_p(q.data_ptr()), m, int(k),
+    _check(L.panda_knn_visits(tree.handle, ctypes.c_void_p(qp), m, int(k),
                               ctypes.c_void_p(ids.data_ptr()), ctypes.c_void_p(d2.data_ptr()),
                               ctypes.c_void_p(vis.data_ptr()), ctypes.c_void_p(stats.data_ptr()),
                               ctypes.byref(prm), _stream_ptr(stream)))

@@ -114,6 +114,41 @@ def test_edge_case_parity(P, case):
                 brute_rows=np.arange(q.shape[0]))
 
 
+def _self_cases():
+    rng = np.random.default_rng(21)
+    w = workloads.uniform_small()
+    yield "uniform_small", w.points, 5, 32
+    yield "n_lt_k", rng.random((5, 2), dtype=np.float32), 9, 4
+    yield "identical", np.full((2000, 3), 0.25, np.float32), 5, 8
+    dup = np.repeat(rng.random((6, 3), dtype=np.float32), 700, axis=0)
+    yield "heavy_dups", dup, 17, 32
+    yield "lattice_ties", workloads.lattice_points(5000, 3, seed=5, side=6), 33, 16
+    yield "gauss_d10", rng.standard_normal((20000, 10)).astype(np.float32), 16, 32
+    yield "gauss_d16_k64", rng.standard_normal((3000, 16)).astype(np.float32), 64, 8
+    yield "cosmo", workloads.cosmology_points(300_000, seed=12, halos=50), 10, 32
+
+
+@pytest.mark.parametrize("case", list(_self_cases()), ids=lambda c: c[0])
+def test_self_query_parity(P, case):
+    """The all-points query equals panda_knn with queries = the points (and the
+    oracle), for both traversal shapes and the blocking and host variants."""
+    import torch
+    name, pts, k, B = case
+    t = P.build(dev(pts), B)
+    ri, rd = gpu_knn(P, t, pts, k)
+    ot = oracle.build(pts, B)
+    eids, ed2 = oracle.knn(ot, pts, k)
+    assert_same_knn(ri, rd, eids, ed2)
+    for trav in ("auto", "per_query"):
+        si, sd = P.knn_self(t, k, traversal=trav)
+        torch.cuda.synchronize()
+        assert_same_knn(si.cpu().numpy(), sd.cpu().numpy(), eids, ed2)
+    si, sd = P.knn_self_sync(t, k)
+    assert_same_knn(si.cpu().numpy(), sd.cpu().numpy(), eids, ed2)
+    hi, hd = P.knn_self_host(t, k)
+    assert_same_knn(hi, hd, eids, ed2)
+
+
 def test_phase_timing_many_levels(P):
     """Phase timing across a build with many level passes (event bookkeeping)."""
     pts = np.random.default_rng(4).random((3_000_000, 3), dtype=np.float32)
@@ -187,6 +222,9 @@ def test_cosmology_self_full_size(P):
     assert np.all(ids[nodup, 0] == np.flatnonzero(nodup))
     ot = oracle.build(w.points, w.bucket)
     treecheck.assert_same_tree(g, ot.export())
+    si, sd = P.knn_self(t, w.k)              # the all-points query: the same rows
+    torch.cuda.synchronize()
+    assert_same_knn(si.cpu().numpy(), sd.cpu().numpy(), ids, d2)
 
 
 def test_sparse_queries_full_size_tree(P):
