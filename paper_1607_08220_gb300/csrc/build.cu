@@ -1069,6 +1069,10 @@ __global__ void k_subtree(BuildArgs a, int wbytes)
             __syncwarp();
         }
     }
+    // the ids left in this warp's pool are holes nothing references: give them
+    // an all-zero header (not a leaf) so a scan of the node table reads no garbage
+    for (int id = pool_next + lane; id < pool_end; id += 32)
+        if (id < a.node_cap) reinterpret_cast<int4*>(a.nodes)[(long long)id * a.ns] = make_int4(0, 0, 0, 0);
     if (lane == 0 && my_nodes) {
         atomicAdd(&a.cnt[kCntRealNodes], my_nodes);
         atomicAdd(&a.cnt[kCntLeaves], my_leaves);

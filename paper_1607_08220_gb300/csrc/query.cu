@@ -291,6 +291,34 @@ panda_status knn_query(const panda_tree* t, const float* queries, int64_t m, int
     return PANDA_OK;
 }
 
+// Jobs of the all-points query: every leaf, in pieces of at most 32 points
+// (one warp each).  Node slots that are not leaves (inner nodes, holes with
+// an all-zero header) are skipped; one atomic per warp of node slots.
+__global__ void k_self_jobs(const float4* nodes, long long slots, int ns, int2* jobs, int* njobs, long long cap,
+                            unsigned* err)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    int start = 0, count = 0;
+    if (i < slots) {
+        const int4 h = __ldg(reinterpret_cast<const int4*>(nodes + i * ns));
+        if (((unsigned)h.w & kMetaLeaf) && h.y > 0) {
+            start = h.x;
+            count = h.y;
+        }
+    }
+    const int nj = (count + 31) >> 5;
+    const int incl = warp_incl_scan(nj);
+    int base = 0;
+    if (lane == 31 && incl > 0) base = atomicAdd(njobs, incl);
+    base = __shfl_sync(kFull, base, 31) + incl - nj;
+    if (base + nj > cap) {
+        atomicOr(err, kErrInternal);
+        return;
+    }
+    for (int j = 0; j < nj; j++) jobs[base + j] = make_int2(start + 32 * j, min(32, count - 32 * j));
+}
+
 panda_status knn_self(const panda_tree* t, int32_t k, int32_t* ids, float* d2, const panda_query_params* params,
                       cudaStream_t stream, unsigned* host_err, int32_t* visits, unsigned long long* stats)
 {
@@ -308,14 +336,26 @@ panda_status knn_self(const panda_tree* t, int32_t k, int32_t* ids, float* d2, c
         return PANDA_ERR_INVALID_ARGUMENT;
     }
     PhaseTimer timer(stream);
-    void* errp = nullptr;
-    panda_status st = ws_alloc(&errp, sizeof(unsigned), stream, "query error word");
+    // scratch: error word, job counter, jobs (at most one per leaf plus one per 32 points)
+    const long long cap = t->num_leaves + t->n / 32 + 1;
+    void* scratch = nullptr;
+    panda_status st = ws_alloc(&scratch, 16 + (size_t)cap * sizeof(int2), stream, "self-query jobs");
     if (st != PANDA_OK) return st;
-    unsigned* err = static_cast<unsigned*>(errp);
-    cudaError_t ce = cudaMemsetAsync(err, 0, sizeof(unsigned), stream);
+    unsigned* err = static_cast<unsigned*>(scratch);
+    int* njobs = reinterpret_cast<int*>(static_cast<char*>(scratch) + 4);
+    int2* jobs = reinterpret_cast<int2*>(static_cast<char*>(scratch) + 16);
+    cudaError_t ce = cudaMemsetAsync(scratch, 0, 16, stream);
     if (ce != cudaSuccess) {
-        ws_free(errp, stream);
+        ws_free(scratch, stream);
         return cuda_fail(ce, "clear query error");
+    }
+    timer.begin("query.jobs");
+    k_self_jobs<<<(unsigned)((t->node_slots + 255) / 256), 256, 0, stream>>>(t->nodes, t->node_slots, t->ns, jobs,
+                                                                          njobs, cap, err);
+    st = note_launch("k_self_jobs");
+    if (st != PANDA_OK) {
+        ws_free(scratch, stream);
+        return st;
     }
     timer.begin("query.traverse");
     KnnArgs ka;
@@ -329,6 +369,9 @@ panda_status knn_self(const panda_tree* t, int32_t k, int32_t* ids, float* d2, c
     ka.num_nodes = t->node_slots;
     ka.npts = t->n;
     ka.self_q = 1;
+    ka.self_jobs = jobs;
+    ka.self_njobs = njobs;
+    ka.self_jobs_cap = cap;
     ka.visits = visits;
     ka.stats = stats;
     ka.transpose_max = (params && params->transpose_max != 0) ? params->transpose_max : 12;
@@ -342,7 +385,7 @@ panda_status knn_self(const panda_tree* t, int32_t k, int32_t* ids, float* d2, c
         if (ce == cudaSuccess) ce = cudaStreamSynchronize(stream);
         if (ce != cudaSuccess) st = cuda_fail(ce, "query");
     }
-    ws_free(errp, stream);
+    ws_free(scratch, stream);
     if (st == PANDA_OK) timer.finish();
     return st;
 }

@@ -95,6 +95,9 @@ struct KnnArgs {
     const KnnReq* reqs;   // (queries / ids / d2 / k above unused; perm lists batch rows)
     int self_q;           // single tree: the queries are the tree's own points, taken in
                           // leaf order from the packed records (queries, perm unused)
+    const int2* self_jobs;   // self_q: warp w takes the packed points [x, x + y) of job w
+    const int* self_njobs;   // (y <= 32: one leaf, or a 32-point piece of a larger one)
+    long long self_jobs_cap; // warps launched for the jobs (their number is at most this)
 };
 
 // Kernel modes: one tree and one query set; one tree and the queries of
@@ -245,14 +248,14 @@ __device__ __forceinline__ void knn_lane_solo(const KnnArgs& a, const KnnSet& S,
 // the kernel holds the packet traversal alone and keeps its registers.  REQS
 // compiles in the per-lane request lookup of sets that span several requests.
 template <int DP, bool SOLO_OK, bool REQS, bool STATS>
-__device__ __forceinline__ void knn_warp_job(const KnnArgs& a, const KnnSet& S, long long g0,
+__device__ __forceinline__ void knn_warp_job(const KnnArgs& a, const KnnSet& S, long long g0, int cnt,
                                              float (*sx)[32], int* sid, unsigned long long* h)
 {
     constexpr int NV = (DP + 1 + 3) / 4;
     constexpr int NS = (4 + 2 * DP + 3) / 4;
     const int lane = threadIdx.x & 31;
     const long long pos = g0 + lane;
-    const bool valid = pos < S.m;
+    const bool valid = lane < cnt && pos < S.m;
     int qi = 0;
     if (valid) qi = S.perm ? S.perm[pos] - S.row_base : (int)pos;
     const float* qsrc = S.queries;
@@ -565,9 +568,18 @@ __global__ void __launch_bounds__(kKnnThreads, knn_min_blocks(DP, MODE, SOLO)) k
         S.nreq = MODE == kKnnOneTreeReqs ? a.nreq : 0;
         S.reqs = a.reqs;
         S.k = a.k;
-        const long long g0 = ((long long)blockIdx.x * (kKnnThreads / 32) + warp) * 32;
+        const long long gw = (long long)blockIdx.x * (kKnnThreads / 32) + warp;
+        long long g0 = gw * 32;
+        int cnt = 32;
+        if (MODE != kKnnOneTreeReqs && a.self_jobs) {
+            // all-points query: one leaf (or a 32-point piece of one) per warp
+            if (gw >= *a.self_njobs) return;
+            const int2 jb = a.self_jobs[gw];
+            g0 = jb.x;
+            cnt = jb.y;
+        }
         if (g0 >= a.m) return;
-        knn_warp_job<DP, SOLO, MODE == kKnnOneTreeReqs, MODE == kKnnStats>(a, S, g0, stage_x[warp],
+        knn_warp_job<DP, SOLO, MODE == kKnnOneTreeReqs, MODE == kKnnStats>(a, S, g0, cnt, stage_x[warp],
                                                                            stage_id[warp], h);
         return;
     }
@@ -579,7 +591,7 @@ __global__ void __launch_bounds__(kKnnThreads, knn_min_blocks(DP, MODE, SOLO)) k
         if (j >= a.njobs) break;
         const KnnJob jb = a.jobs[j];
         const KnnSet S = a.sets[jb.set];
-        knn_warp_job<DP, SOLO, true, false>(a, S, jb.pos, stage_x[warp], stage_id[warp], h);
+        knn_warp_job<DP, SOLO, true, false>(a, S, jb.pos, 32, stage_x[warp], stage_id[warp], h);
         __syncwarp();
     }
 }
