@@ -85,7 +85,7 @@ panda_status launch_knn_dp(const KnnArgs& a, cudaStream_t s)
         return a.solo ? launch_knn_multi<DP, true>(a, heap_bytes, s) : launch_knn_multi<DP, false>(a, heap_bytes, s);
     }
     // one launch per tree: one warp per 32 queries (all-points query: per job)
-    const long long warps = a.self_jobs ? a.self_jobs_cap : (a.m + 31) / 32;
+    const long long warps = a.pos_jobs ? a.pos_jobs_cap : (a.m + 31) / 32;
     const long long blocks = (warps + kKnnThreads / 32 - 1) / (kKnnThreads / 32);
     if (blocks <= 0) return PANDA_OK;
     if (a.stats || a.visits) {

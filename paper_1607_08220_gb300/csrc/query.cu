@@ -144,6 +144,32 @@ __global__ void k_order_scatter(const unsigned* keys, long long m, int* cursor, 
     perm[p] = (int)i;
 }
 
+// Jobs of a leaf-ordered query set: the queries of each bin (after the
+// counting sort, bin b holds positions [end(b - 1), end(b)), end(b) =
+// bsum[b >> 12] + cursor[b]), in pieces of at most 32.  One atomic per warp.
+__global__ void k_bin_jobs(const int* cursor, const int* bsum, int nb, int2* jobs, int* njobs, long long cap,
+                           unsigned* err)
+{
+    const long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    int start = 0, count = 0;
+    if (b < nb) {
+        const int end = bsum[b >> 12] + cursor[b];
+        start = b > 0 ? bsum[(b - 1) >> 12] + cursor[b - 1] : 0;
+        count = end - start;
+    }
+    const int nj = (count + 31) >> 5;
+    const int incl = warp_incl_scan(nj);
+    int base = 0;
+    if (lane == 31 && incl > 0) base = atomicAdd(njobs, incl);
+    base = __shfl_sync(kFull, base, 31) + incl - nj;
+    if (base + nj > cap) {
+        atomicOr(err, kErrInternal);
+        return;
+    }
+    for (int j = 0; j < nj; j++) jobs[base + j] = make_int2(start + 32 * j, min(32, count - 32 * j));
+}
+
 template <int DP>
 panda_status launch_knn_dp(const KnnArgs& a, cudaStream_t s);
 
@@ -202,6 +228,15 @@ panda_status knn_query(const panda_tree* t, const float* queries, int64_t m, int
     cudaError_t ce = cudaMemsetAsync(err, 0, sizeof(unsigned), stream);
     if (ce != cudaSuccess) return cleanup(), cuda_fail(ce, "clear query error");
     int* perm = nullptr;
+    const int traversal = params ? params->traversal : PANDA_TRAVERSAL_AUTO;
+    const int solo = traversal == PANDA_TRAVERSAL_PER_QUERY ? 1
+                     : traversal == PANDA_TRAVERSAL_PACKET  ? 0
+                                                            : prefer_per_query(m, t->n, t->d);
+    // dense leaf-ordered packets: one leaf's queries per warp (as the
+    // all-points query), so no packet straddles two leaves
+    int2* jobs = nullptr;
+    int* njobs = nullptr;
+    long long jobs_cap = 0;
     if (order != PANDA_ORDER_NONE && m > 32) {
         timer.begin("query.order");
         OrderArgs oa;
@@ -253,6 +288,17 @@ panda_status knn_query(const panda_tree* t, const float* queries, int64_t m, int
         if ((st = note_launch("k_scan_sums")) != PANDA_OK) return cleanup(), st;
         k_order_scatter<<<gb, 256, 0, stream>>>(keys, m, hist, bsum, perm);
         if ((st = note_launch("k_order_scatter")) != PANDA_OK) return cleanup(), st;
+        if (order == PANDA_ORDER_LEAF && !solo && 2 * m >= t->n) {
+            jobs_cap = nb + m / 32 + 1;
+            void* jp = nullptr;
+            if ((st = get(&jp, 16 + (size_t)jobs_cap * sizeof(int2), "query jobs")) != PANDA_OK) return cleanup(), st;
+            njobs = static_cast<int*>(jp);
+            jobs = reinterpret_cast<int2*>(static_cast<char*>(jp) + 16);
+            ce = cudaMemsetAsync(njobs, 0, sizeof(int), stream);
+            if (ce != cudaSuccess) return cleanup(), cuda_fail(ce, "clear query jobs");
+            k_bin_jobs<<<(unsigned)((nb + 255) / 256), 256, 0, stream>>>(hist, bsum, nb, jobs, njobs, jobs_cap, err);
+            if ((st = note_launch("k_bin_jobs")) != PANDA_OK) return cleanup(), st;
+        }
     }
     timer.begin("query.traverse");
     KnnArgs ka;
@@ -270,12 +316,10 @@ panda_status knn_query(const panda_tree* t, const float* queries, int64_t m, int
     ka.visits = visits;
     ka.stats = stats;
     ka.transpose_max = (params && params->transpose_max != 0) ? params->transpose_max : 12;
-    {
-        const int tr = params ? params->traversal : PANDA_TRAVERSAL_AUTO;
-        ka.solo = tr == PANDA_TRAVERSAL_PER_QUERY ? 1
-                  : tr == PANDA_TRAVERSAL_PACKET  ? 0
-                                                  : prefer_per_query(m, t->n, t->d);
-    }
+    ka.solo = solo;
+    ka.pos_jobs = jobs;
+    ka.pos_njobs = njobs;
+    ka.pos_jobs_cap = jobs_cap;
     ka.d = t->d;
     ka.k = k;
     st = launch_knn(ka, t->dp, stream);
@@ -294,7 +338,7 @@ panda_status knn_query(const panda_tree* t, const float* queries, int64_t m, int
 // Jobs of the all-points query: every leaf, in pieces of at most 32 points
 // (one warp each).  Node slots that are not leaves (inner nodes, holes with
 // an all-zero header) are skipped; one atomic per warp of node slots.
-__global__ void k_self_jobs(const float4* nodes, long long slots, int ns, int2* jobs, int* njobs, long long cap,
+__global__ void k_pos_jobs(const float4* nodes, long long slots, int ns, int2* jobs, int* njobs, long long cap,
                             unsigned* err)
 {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -350,9 +394,9 @@ panda_status knn_self(const panda_tree* t, int32_t k, int32_t* ids, float* d2, c
         return cuda_fail(ce, "clear query error");
     }
     timer.begin("query.jobs");
-    k_self_jobs<<<(unsigned)((t->node_slots + 255) / 256), 256, 0, stream>>>(t->nodes, t->node_slots, t->ns, jobs,
+    k_pos_jobs<<<(unsigned)((t->node_slots + 255) / 256), 256, 0, stream>>>(t->nodes, t->node_slots, t->ns, jobs,
                                                                           njobs, cap, err);
-    st = note_launch("k_self_jobs");
+    st = note_launch("k_pos_jobs");
     if (st != PANDA_OK) {
         ws_free(scratch, stream);
         return st;
@@ -369,9 +413,9 @@ panda_status knn_self(const panda_tree* t, int32_t k, int32_t* ids, float* d2, c
     ka.num_nodes = t->node_slots;
     ka.npts = t->n;
     ka.self_q = 1;
-    ka.self_jobs = jobs;
-    ka.self_njobs = njobs;
-    ka.self_jobs_cap = cap;
+    ka.pos_jobs = jobs;
+    ka.pos_njobs = njobs;
+    ka.pos_jobs_cap = cap;
     ka.visits = visits;
     ka.stats = stats;
     ka.transpose_max = (params && params->transpose_max != 0) ? params->transpose_max : 12;

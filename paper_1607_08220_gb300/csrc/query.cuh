@@ -95,9 +95,9 @@ struct KnnArgs {
     const KnnReq* reqs;   // (queries / ids / d2 / k above unused; perm lists batch rows)
     int self_q;           // single tree: the queries are the tree's own points, taken in
                           // leaf order from the packed records (queries, perm unused)
-    const int2* self_jobs;   // self_q: warp w takes the packed points [x, x + y) of job w
-    const int* self_njobs;   // (y <= 32: one leaf, or a 32-point piece of a larger one)
-    long long self_jobs_cap; // warps launched for the jobs (their number is at most this)
+    const int2* pos_jobs;    // warp w takes the positions [x, x + y) of job w (y <= 32):
+    const int* pos_njobs;    // one leaf's queries, or a 32-query piece of them
+    long long pos_jobs_cap;  // warps launched for the jobs (their number is at most this)
 };
 
 // Kernel modes: one tree and one query set; one tree and the queries of
@@ -571,10 +571,10 @@ __global__ void __launch_bounds__(kKnnThreads, knn_min_blocks(DP, MODE, SOLO)) k
         const long long gw = (long long)blockIdx.x * (kKnnThreads / 32) + warp;
         long long g0 = gw * 32;
         int cnt = 32;
-        if (MODE != kKnnOneTreeReqs && a.self_jobs) {
-            // all-points query: one leaf (or a 32-point piece of one) per warp
-            if (gw >= *a.self_njobs) return;
-            const int2 jb = a.self_jobs[gw];
+        if (MODE != kKnnOneTreeReqs && a.pos_jobs) {
+            // one leaf's queries (or a 32-query piece of them) per warp
+            if (gw >= *a.pos_njobs) return;
+            const int2 jb = a.pos_jobs[gw];
             g0 = jb.x;
             cnt = jb.y;
         }
