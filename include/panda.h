@@ -75,7 +75,7 @@ typedef struct panda_query_params {
     int32_t transpose_max;  /* scan shape: a leaf bucket needed by at most this many of
                                a warp's 32 queries is scanned with lanes holding points
                                (queries broadcast in turn), otherwise with lanes holding
-                               queries; 0 = default (12), 32 = always the former,
+                               queries; 0 = default (16), 32 = always the former,
                                -1 = always the latter.  Never changes results. */
     int32_t traversal;      /* PANDA_TRAVERSAL_*: 0 = automatic (per-query when the
                                queries are sparse, fewer than n/4, and d <= 4), never

@@ -48,7 +48,7 @@ struct panda_batch {
     unsigned* d_err = nullptr;
     cudaGraphExec_t exec = nullptr;
     int64_t kernels_per_run = 0;
-    int transpose_max = 12;
+    int transpose_max = panda::kTransposeMaxDefault;
     int traversal = PANDA_TRAVERSAL_AUTO;
     int any_solo = 0;   // some set takes the per-query traversal
     std::vector<void*> owned;
@@ -318,7 +318,7 @@ panda_status panda_batch_set_query_params(panda_batch* b, const panda_query_para
         cudaGraphExecDestroy(b->exec);
         b->exec = nullptr;
     }
-    b->transpose_max = (params && params->transpose_max != 0) ? params->transpose_max : 12;
+    b->transpose_max = (params && params->transpose_max != 0) ? params->transpose_max : panda::kTransposeMaxDefault;
     b->traversal = params ? params->traversal : PANDA_TRAVERSAL_AUTO;
     // rewrite the set descriptors with the requested traversal shape
     std::vector<KnnSet> hs(b->nsets);

@@ -17,6 +17,10 @@ constexpr int kMaxDepth = 64;      // deepest level allowed below the root
 constexpr int kMaxDim = 16;
 constexpr int kMaxBucket = 256;
 constexpr int kMaxK = 64;
+// Default scan-shape switch of the packet traversal: a bucket needed by at most
+// this many of a warp's lanes is scanned lanes = points (measured best between
+// 12 and 24 on 3-D self-KNN and 10-D queries; 16 on both).
+constexpr int kTransposeMaxDefault = 16;
 constexpr int kTile = 16384;       // points per level-stage tile (multiple of 4)
 constexpr unsigned kFull = 0xffffffffu;
 

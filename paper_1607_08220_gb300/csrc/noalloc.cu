@@ -170,7 +170,7 @@ extern "C" panda_status panda_knn_noalloc(const panda_tree* t, const float* quer
     ka.npts = t->n;
     ka.d = t->d;
     ka.k = k;
-    ka.transpose_max = 12;
+    ka.transpose_max = kTransposeMaxDefault;
     ka.solo = prefer_per_query(m, t->n, t->d);
     return launch_traversal(ka, t->dp, s);
 }

@@ -315,7 +315,7 @@ panda_status knn_query(const panda_tree* t, const float* queries, int64_t m, int
     ka.npts = t->n;
     ka.visits = visits;
     ka.stats = stats;
-    ka.transpose_max = (params && params->transpose_max != 0) ? params->transpose_max : 12;
+    ka.transpose_max = (params && params->transpose_max != 0) ? params->transpose_max : kTransposeMaxDefault;
     ka.solo = solo;
     ka.pos_jobs = jobs;
     ka.pos_njobs = njobs;
@@ -418,7 +418,7 @@ panda_status knn_self(const panda_tree* t, int32_t k, int32_t* ids, float* d2, c
     ka.pos_jobs_cap = cap;
     ka.visits = visits;
     ka.stats = stats;
-    ka.transpose_max = (params && params->transpose_max != 0) ? params->transpose_max : 12;
+    ka.transpose_max = (params && params->transpose_max != 0) ? params->transpose_max : kTransposeMaxDefault;
     ka.solo = (params && params->traversal == PANDA_TRAVERSAL_PER_QUERY) ? 1 : 0;
     ka.d = t->d;
     ka.k = k;

@@ -297,7 +297,7 @@ panda_status enqueue_batch(Server* S, const std::vector<Request*>& batch_in, InF
             ka.m = m_total;
             ka.d = S->trees[group_tree[0]]->d;
             ka.k = kmax;
-            ka.transpose_max = 12;
+            ka.transpose_max = kTransposeMaxDefault;
             ka.solo = any_solo;
             switch (S->trees[group_tree[0]]->dp) {
                 case 2: st = launch_knn_dp<2>(ka, s); break;
@@ -323,7 +323,7 @@ panda_status enqueue_batch(Server* S, const std::vector<Request*>& batch_in, InF
             ka.m = group_m[g];
             ka.d = t->d;
             ka.k = group_kmax[g];
-            ka.transpose_max = 12;
+            ka.transpose_max = kTransposeMaxDefault;
             ka.solo = prefer_per_query(group_m[g], t->n, t->d);
             ka.reqs = d_kr + group_req0[g];
             ka.nreq = (int)groups[g].size();
