@@ -336,26 +336,42 @@ panda_status knn_query(const panda_tree* t, const float* queries, int64_t m, int
 }
 
 // Jobs of the all-points query: every leaf, in pieces of at most 32 points
-// (one warp each).  Node slots that are not leaves (inner nodes, holes with
-// an all-zero header) are skipped; one atomic per warp of node slots.
-__global__ void k_pos_jobs(const float4* nodes, long long slots, int ns, int2* jobs, int* njobs, long long cap,
-                            unsigned* err)
+// (one warp each), listed in position order to 1,024-point granularity so the
+// warps in flight at any time work on one region of the tree (L2 reuse): a
+// counting sort of the leaves by start >> 10.  Node slots that are not leaves
+// (inner nodes, holes with an all-zero header) are skipped.
+__device__ __forceinline__ bool leaf_of_slot(const float4* nodes, long long i, int ns, int& start, int& count)
+{
+    const int4 h = __ldg(reinterpret_cast<const int4*>(nodes + i * ns));
+    start = h.x;
+    count = h.y;
+    return ((unsigned)h.w & kMetaLeaf) && h.y > 0;
+}
+
+// Pass 1: jobs per 1,024-position bin, and the total (one atomic per warp).
+__global__ void k_pos_jobs_count(const float4* nodes, long long slots, int ns, int* hist, int* njobs)
 {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const int lane = threadIdx.x & 31;
-    int start = 0, count = 0;
-    if (i < slots) {
-        const int4 h = __ldg(reinterpret_cast<const int4*>(nodes + i * ns));
-        if (((unsigned)h.w & kMetaLeaf) && h.y > 0) {
-            start = h.x;
-            count = h.y;
-        }
+    int start = 0, count = 0, nj = 0;
+    if (i < slots && leaf_of_slot(nodes, i, ns, start, count)) {
+        nj = (count + 31) >> 5;
+        atomicAdd(&hist[start >> 10], nj);
     }
+    const int tot = warp_sum(nj);
+    if ((threadIdx.x & 31) == 0 && tot > 0) atomicAdd(njobs, tot);
+}
+
+// Pass 2 (after the scan of hist into cursor offsets + bsum): place each
+// leaf's jobs at its bin's next free slots.
+__global__ void k_pos_jobs_place(const float4* nodes, long long slots, int ns, int* cursor, const int* bsum,
+                                 int2* jobs, long long cap, unsigned* err)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    int start = 0, count = 0;
+    if (i >= slots || !leaf_of_slot(nodes, i, ns, start, count)) return;
     const int nj = (count + 31) >> 5;
-    const int incl = warp_incl_scan(nj);
-    int base = 0;
-    if (lane == 31 && incl > 0) base = atomicAdd(njobs, incl);
-    base = __shfl_sync(kFull, base, 31) + incl - nj;
+    const int key = start >> 10;
+    const long long base = (long long)atomicAdd(&cursor[key], nj) + bsum[key >> 12];
     if (base + nj > cap) {
         atomicOr(err, kErrInternal);
         return;
@@ -380,23 +396,43 @@ panda_status knn_self(const panda_tree* t, int32_t k, int32_t* ids, float* d2, c
         return PANDA_ERR_INVALID_ARGUMENT;
     }
     PhaseTimer timer(stream);
-    // scratch: error word, job counter, jobs (at most one per leaf plus one per 32 points)
+    // scratch: error word, job counter, jobs (at most one per leaf plus one per
+    // 32 points), the bin histogram (bins of 1,024 positions) and its block sums
     const long long cap = t->num_leaves + t->n / 32 + 1;
+    const int nb = (int)(t->n >> 10) + 1;
+    const int nblk = (nb + 4095) / 4096;
+    const size_t hist_off = 16 + (size_t)cap * sizeof(int2);
+    const size_t bytes = hist_off + ((size_t)nblk * 4096 + nblk) * sizeof(int);
     void* scratch = nullptr;
-    panda_status st = ws_alloc(&scratch, 16 + (size_t)cap * sizeof(int2), stream, "self-query jobs");
+    panda_status st = ws_alloc(&scratch, bytes, stream, "self-query jobs");
     if (st != PANDA_OK) return st;
     unsigned* err = static_cast<unsigned*>(scratch);
     int* njobs = reinterpret_cast<int*>(static_cast<char*>(scratch) + 4);
     int2* jobs = reinterpret_cast<int2*>(static_cast<char*>(scratch) + 16);
+    int* hist = reinterpret_cast<int*>(static_cast<char*>(scratch) + hist_off);
+    int* bsum = hist + (size_t)nblk * 4096;
     cudaError_t ce = cudaMemsetAsync(scratch, 0, 16, stream);
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(hist, 0, (size_t)nb * sizeof(int), stream);
     if (ce != cudaSuccess) {
         ws_free(scratch, stream);
         return cuda_fail(ce, "clear query error");
     }
     timer.begin("query.jobs");
-    k_pos_jobs<<<(unsigned)((t->node_slots + 255) / 256), 256, 0, stream>>>(t->nodes, t->node_slots, t->ns, jobs,
-                                                                          njobs, cap, err);
-    st = note_launch("k_pos_jobs");
+    const unsigned gs = (unsigned)((t->node_slots + 255) / 256);
+    k_pos_jobs_count<<<gs, 256, 0, stream>>>(t->nodes, t->node_slots, t->ns, hist, njobs);
+    st = note_launch("k_pos_jobs_count");
+    if (st == PANDA_OK) {
+        k_scan_blocks<<<nblk, 1024, 0, stream>>>(hist, nb, bsum);
+        st = note_launch("k_scan_blocks");
+    }
+    if (st == PANDA_OK) {
+        k_scan_sums<<<1, 1024, 0, stream>>>(bsum, nblk);
+        st = note_launch("k_scan_sums");
+    }
+    if (st == PANDA_OK) {
+        k_pos_jobs_place<<<gs, 256, 0, stream>>>(t->nodes, t->node_slots, t->ns, hist, bsum, jobs, cap, err);
+        st = note_launch("k_pos_jobs_place");
+    }
     if (st != PANDA_OK) {
         ws_free(scratch, stream);
         return st;
