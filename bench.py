@@ -214,12 +214,12 @@ def run_reference(args):
 
 # DRAM traffic of the packet traversal kernel (k_knn, d = 3, k = 10, all-points
 # query) per query: dram__bytes_read.sum + dram__bytes_write.sum of one ncu
-# capture on the cosmology self-KNN at n = m = 2^23 (1.184872 GB + 1.496198 GB),
+# capture on the cosmology self-KNN at n = m = 2^23 (1.177537 GB + 1.490322 GB),
 # scaled to a full launch by the number of queries.  It describes the kernel as
 # committed with profiles/k_knn_cosmology_n8388608.md and must be re-captured
 # (or dropped) whenever that kernel changes.
 KNN_TRAFFIC = {"workload": "cosmology_self", "path": "self", "d": 3, "k": 10,
-               "bytes_per_query": (1.184872e9 + 1.496198e9) / 2 ** 23,
+               "bytes_per_query": (1.177537e9 + 1.490322e9) / 2 ** 23,
                "source": "ncu capture at n = m = 2^23, scaled by queries (profiles/k_knn_cosmology_n8388608.md)"}
 
 
