@@ -1137,15 +1137,15 @@ int subtree_threshold(int d, int bucket)
 
 panda_status configure_kernels()
 {
-    static bool done = false;
-    if (done) return PANDA_OK;
-    PANDA_CUDA(cudaFuncSetAttribute(k_sample, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    kMaxDim * kSamples * 4),
-               "configure k_sample");
-    PANDA_CUDA(cudaFuncSetAttribute(k_subtree, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024),
-               "configure k_subtree");
-    done = true;
-    return PANDA_OK;
+    static PerDeviceOnce once;
+    return once_per_device(once, [] {
+        PANDA_CUDA(cudaFuncSetAttribute(k_sample, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        kMaxDim * kSamples * 4),
+                   "configure k_sample");
+        PANDA_CUDA(cudaFuncSetAttribute(k_subtree, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024),
+                   "configure k_subtree");
+        return PANDA_OK;
+    });
 }
 
 struct Plan {

@@ -42,8 +42,8 @@ panda_status fill_multi_blocks()
 template <int DP>
 panda_status configure_knn()
 {
-    static bool configured = false;
-    if (!configured) {
+    static PerDeviceOnce once;
+    return once_per_device(once, [] {
         panda_status st = configure_knn_variant<DP, kKnnOneSet, false>();
         if (st == PANDA_OK) st = configure_knn_variant<DP, kKnnOneSet, true>();
         if (st == PANDA_OK) st = configure_knn_variant<DP, kKnnOneTreeReqs, false>();
@@ -54,10 +54,8 @@ panda_status configure_knn()
         if (st == PANDA_OK) st = configure_knn_variant<DP, kKnnStats, true>();
         if (st == PANDA_OK) st = fill_multi_blocks<DP, false>();
         if (st == PANDA_OK) st = fill_multi_blocks<DP, true>();
-        if (st != PANDA_OK) return st;
-        configured = true;
-    }
-    return PANDA_OK;
+        return st;
+    });
 }
 
 // Persistent launch of the multi-set kernel: as many blocks as can be resident.

@@ -6,6 +6,8 @@
 #include <stdint.h>
 
 #include <string>
+#include <atomic>
+#include <mutex>
 #include <vector>
 
 #include "panda.h"
@@ -57,6 +59,26 @@ struct PhaseTimer {
 bool phase_timing_enabled();
 // While set on this thread, PhaseTimers record nothing (used around graph capture).
 void set_phase_timing_suppressed(bool on);
+// Runs fn once for the current device (kernel attributes are per device);
+// thread-safe.  A failed fn is retried on the next call.
+constexpr int kMaxDevices = 64;
+struct PerDeviceOnce {
+    std::mutex mu;
+    std::atomic<bool> done[kMaxDevices] = {};
+};
+template <class F>
+panda_status once_per_device(PerDeviceOnce& o, F fn)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return fn();
+    if (o.done[dev].load(std::memory_order_acquire)) return PANDA_OK;
+    std::lock_guard<std::mutex> lk(o.mu);
+    if (o.done[dev].load(std::memory_order_relaxed)) return PANDA_OK;
+    const panda_status st = fn();
+    if (st == PANDA_OK) o.done[dev].store(true, std::memory_order_release);
+    return st;
+}
+
 // Launch attributes of the traversal kernels (set before any graph capture).
 panda_status configure_knn_lo();
 panda_status configure_knn_hi();
