@@ -42,7 +42,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=["cosmology_self", "uniform_small", "features_10d", "batched_sets",
-                                           "plasma_serving", "features_10d_served"],
+                                           "plasma_serving", "features_10d_served", "features_10d_classify"],
                     default="cosmology_self")
     ap.add_argument("--duration", type=float, default=1.0, help="seconds of the served request stream")
     ap.add_argument("--nsets", type=int, default=512, help="sets of the batched workload")
@@ -67,6 +67,15 @@ def workload(name: str, n: int = 0):
     if name == "uniform_small":
         return workloads.uniform_small()
     return workloads.features_10d()
+
+
+def rule_labels(x: np.ndarray) -> np.ndarray:
+    """Synthetic 3-class labels of 10-D feature rows (the paper's Daya Bay study
+    classifies 10-D encodings into 3 event classes; its labels are not public):
+    a fixed rule on two coordinates, so a KNN vote can recover it."""
+    a = (x[:, 0] > 0).astype(np.int32)
+    b = (x[:, 1] > 0.2).astype(np.int32)
+    return np.minimum(a + 2 * b, 2).astype(np.int32)
 
 
 def workload_config(w, order):
@@ -298,11 +307,18 @@ def run_ours(args):
     if args.query_path == "self" and not self_q:
         raise SystemExit("--query-path self needs a workload whose queries are its points")
 
+    classify = args.workload == "features_10d_classify"
+    if classify:
+        lab_dev = torch.from_numpy(rule_labels(w.points)).cuda()
+        pred = torch.empty(m, dtype=torch.int32, device="cuda")
+
     def query(t):
         if use_self:
             P.knn_self(t, k, out=(ids, d2))
         else:
             P.knn(t, q_dev, k, order=args.order, out=(ids, d2))
+        if classify:
+            P.knn_vote(ids, lab_dev, out=pred)
 
     def step():
         t = P.build(pts_dev, B)
@@ -478,6 +494,11 @@ def run_ours(args):
             "build_ms": build_ms, "query_ms": query_ms,
             "phases_ms_per_step": {nm: round(v[0], 4) for nm, v in per_step.items()},
             "tree": {"nodes": info["num_nodes"], "leaves": info["num_leaves"], "depth": info["depth"]}}
+    if classify:
+        acc = float((pred.cpu().numpy() == rule_labels(w.queries)).mean())
+        line["classification"] = {"rule": "label = min((x0 > 0) + 2 (x1 > 0.2), 2) on the 10-D features",
+                                  "classes": 3, "k": k, "accuracy": acc,
+                                  "step": "build + KNN + majority vote (panda_knn_vote) per step"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

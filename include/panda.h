@@ -154,6 +154,21 @@ panda_status panda_knn_self_async(const panda_tree* tree, int32_t k, int32_t* ou
 panda_status panda_knn_self_host(const panda_tree* tree, int32_t k, int32_t* out_ids, float* out_d2,
                                  const panda_query_params* params, void* stream);
 
+/* ---- prediction from a KNN result (Sec. I: majority vote for classification,
+ * average for regression) ----------------------------------------------------
+ * ids: device [m][k] int32 as written by a query on a tree of n points (entries
+ * outside [0, n), such as the -1 padding, are ignored).  labels / values:
+ * device [n], indexed by point id.  Per row: panda_knn_vote writes the label
+ * with the largest count among the valid neighbours (the smallest label among
+ * equal counts; -1 when there is none); panda_knn_mean writes the FP32 sum of
+ * their values in rank order (nearest first, from +0) divided in FP32 by their
+ * number (NaN when there is none).  Both only enqueue on `stream`.  No
+ * counterpart in the paper's code: it names these uses of the neighbours. */
+panda_status panda_knn_vote(const int32_t* ids, int64_t m, int32_t k, const int32_t* labels, int64_t n,
+                            int32_t* out_labels, void* stream);
+panda_status panda_knn_mean(const int32_t* ids, int64_t m, int32_t k, const float* values, int64_t n,
+                            float* out_values, void* stream);
+
 /* Same query as panda_knn_async (default parameters) for callers that cannot
  * allocate device memory while they query.  No counterpart in the paper: the
  * query ordering's scratch space is a fixed file-scope device array (12.6 MB,

@@ -33,6 +33,8 @@ SIGNATURES = {
     "panda_knn_async": ([_P, _P, _I64, _I32, _P, _P, _P, _P], ctypes.c_int),
     "panda_knn_host": ([_P, _P, _I64, _I32, _P, _P, _P, _P], ctypes.c_int),
     "panda_knn_self": ([_P, _I32, _P, _P], ctypes.c_int),
+    "panda_knn_vote": ([_P, _I64, _I32, _P, _I64, _P, _P], ctypes.c_int),
+    "panda_knn_mean": ([_P, _I64, _I32, _P, _I64, _P, _P], ctypes.c_int),
     "panda_knn_self_async": ([_P, _I32, _P, _P, _P, _P], ctypes.c_int),
     "panda_knn_self_host": ([_P, _I32, _P, _P, _P, _P], ctypes.c_int),
     "panda_knn_visits": ([_P, _P, _I64, _I32, _P, _P, _P, _P, _P, _P], ctypes.c_int),
@@ -486,6 +488,32 @@ def knn_self_host(tree: Tree, k: int, stream=None, out: tuple | None = None):
     _check(L.panda_knn_self_host(tree.handle, int(k), ids.ctypes.data_as(ctypes.c_void_p),
                                  d2.ctypes.data_as(ctypes.c_void_p), ctypes.byref(prm), _stream_ptr(stream)))
     return ids, d2
+
+
+def knn_vote(ids, labels, stream=None, out=None):
+    """Majority label of each row of a KNN result (Sec. I): ids int32 [m][k] and
+    labels int32 [n] CUDA tensors; returns int32 [m] (-1: no valid neighbour)."""
+    torch = _torch()
+    L = load()
+    m, k = ids.shape
+    if out is None:
+        out = torch.empty(m, dtype=torch.int32, device=ids.device)
+    _check(L.panda_knn_vote(ctypes.c_void_p(ids.data_ptr()), m, k, ctypes.c_void_p(labels.data_ptr()),
+                            labels.shape[0], ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)))
+    return out
+
+
+def knn_mean(ids, values, stream=None, out=None):
+    """Mean of the neighbours' values (FP32, rank order) of each row of a KNN
+    result (Sec. I regression); returns float32 [m] (NaN: no valid neighbour)."""
+    torch = _torch()
+    L = load()
+    m, k = ids.shape
+    if out is None:
+        out = torch.empty(m, dtype=torch.float32, device=ids.device)
+    _check(L.panda_knn_mean(ctypes.c_void_p(ids.data_ptr()), m, k, ctypes.c_void_p(values.data_ptr()),
+                            values.shape[0], ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)))
+    return out
 
 
 def knn_visits(tree: Tree, queries, k: int, order: str = "leaf", stream=None, transpose_max: int = 0):
