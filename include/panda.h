@@ -80,6 +80,11 @@ typedef struct panda_query_params {
     int32_t traversal;      /* PANDA_TRAVERSAL_*: 0 = automatic (per-query when the
                                queries are sparse, fewer than n/4, and d <= 4), never
                                changes results */
+    int32_t bounded;        /* 1: Algorithm 1's search radius r applies -- only points
+                               with d2 <= max_d2 (= r^2, FP32) are neighbours; rows
+                               with fewer than k pad with (-1, +inf).  Not with
+                               panda_knn_visits (PANDA_ERR_UNSUPPORTED). */
+    float max_d2;           /* >= 0 (NaN is invalid); used when bounded = 1 */
     int32_t reserved;
 } panda_query_params;
 

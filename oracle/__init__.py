@@ -82,8 +82,12 @@ def _load():
         L.or_tree_export.restype = None
         L.or_knn.argtypes = [P, P, i64, i32, P, P, P, i32]
         L.or_knn.restype = ctypes.c_int
+        L.or_knn_r.argtypes = [P, P, i64, i32, ctypes.c_float, P, P, P, i32]
+        L.or_knn_r.restype = ctypes.c_int
         L.or_brute_knn.argtypes = [P, i64, i32, P, i64, i32, P, P, i32]
         L.or_brute_knn.restype = ctypes.c_int
+        L.or_brute_knn_r.argtypes = [P, i64, i32, P, i64, i32, ctypes.c_float, P, P, i32]
+        L.or_brute_knn_r.restype = ctypes.c_int
         L.or_brute_knn_rows.argtypes = [P, i64, i32, P, P, i64, i32, P, P, i32]
         L.or_brute_knn_rows.restype = ctypes.c_int
         L.or_max_depth.restype = i32
@@ -158,8 +162,9 @@ def build(points: np.ndarray, bucket: int = 32) -> Tree:
     return Tree(h, n, d, bucket)
 
 
-def knn(tree: Tree, queries: np.ndarray, k: int, threads: int = 0, visits: bool = False):
-    """Algorithm 1 (corrected) for every query row; returns (ids, d2[, visits])."""
+def knn(tree: Tree, queries: np.ndarray, k: int, threads: int = 0, visits: bool = False, max_d2=None):
+    """Algorithm 1 (corrected) for every query row; returns (ids, d2[, visits]).
+    max_d2: Algorithm 1's radius r, squared (neighbours with d2 <= max_d2 only)."""
     q = np.ascontiguousarray(queries, dtype=np.float32)
     m = q.shape[0]
     if q.ndim != 2 or (m and q.shape[1] != tree.d):
@@ -167,17 +172,28 @@ def knn(tree: Tree, queries: np.ndarray, k: int, threads: int = 0, visits: bool 
     ids = np.empty((m, k), np.int32)
     d2 = np.empty((m, k), np.float32)
     v = np.empty((m, 2), np.int64) if visits else None
-    _check(_lib.or_knn(tree._h, _ptr(q), m, int(k), _ptr(ids), _ptr(d2),
-                       _ptr(v) if v is not None else None, int(threads)))
+    r2 = np.float32(np.inf if max_d2 is None else max_d2)
+    _check(_lib.or_knn_r(tree._h, _ptr(q), m, int(k), ctypes.c_float(r2), _ptr(ids), _ptr(d2),
+                         _ptr(v) if v is not None else None, int(threads)))
     return (ids, d2, v) if visits else (ids, d2)
 
 
-def brute_knn(points: np.ndarray, queries: np.ndarray, k: int, threads: int = 0, rows=None):
-    """Exhaustive KNN (the plain definition).  ``rows`` selects query rows."""
+def brute_knn(points: np.ndarray, queries: np.ndarray, k: int, threads: int = 0, rows=None, max_d2=None):
+    """Exhaustive KNN (the plain definition).  ``rows`` selects query rows;
+    ``max_d2`` keeps only points with d2 <= max_d2."""
     L = _load()
     pts = np.ascontiguousarray(points, dtype=np.float32)
     q = np.ascontiguousarray(queries, dtype=np.float32)
     n, d = pts.shape
+    if max_d2 is not None:
+        if rows is not None:
+            q = q[np.asarray(rows)]
+        m = q.shape[0]
+        ids = np.empty((m, k), np.int32)
+        d2 = np.empty((m, k), np.float32)
+        _check(L.or_brute_knn_r(_ptr(pts), n, d, _ptr(q), m, int(k), ctypes.c_float(np.float32(max_d2)),
+                                _ptr(ids), _ptr(d2), int(threads)))
+        return ids, d2
     if rows is None:
         m = q.shape[0]
         ids = np.empty((m, k), np.int32)

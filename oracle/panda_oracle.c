@@ -447,8 +447,11 @@ static void write_row(const float *hd, const int32_t *hid, int32_t cnt, int32_t 
     }
 }
 
-/* Algorithm 1 (corrected) for one query; visits = {nodes processed, points scanned}. */
-static void find_knn(const or_tree *t, const float *q, int32_t k, float *hd, int32_t *hid,
+/* Algorithm 1 (corrected) for one query; visits = {nodes processed, points scanned}.
+ * r2: Algorithm 1's search radius r, squared (reading R11: only points with
+ * d2 <= r2 are neighbours; +inf = unbounded).  Until k neighbours are held,
+ * r' = r2. */
+static void find_knn(const or_tree *t, const float *q, int32_t k, float r2, float *hd, int32_t *hid,
                      int32_t *cnt, int64_t *visits)
 {
     const int d = t->d;
@@ -463,7 +466,7 @@ static void find_knn(const or_tree *t, const float *q, int32_t k, float *hd, int
         sp--;
         int64_t node = stack_node[sp];
         float bound = stack_bound[sp];
-        float rk = (*cnt < k) ? INFINITY : hd[k - 1];    /* r' */
+        float rk = (*cnt < k) ? r2 : hd[k - 1];          /* r' */
         if (bound > rk) continue;                        /* C3: prune only if strictly farther */
         const or_node *nd = &t->nodes[node];
         if (visits) visits[0]++;
@@ -472,6 +475,7 @@ static void find_knn(const or_tree *t, const float *q, int32_t k, float *hd, int
                 int32_t id = t->perm[i];
                 float dv = sq_dist(q, t->pts + (int64_t)id * d, d);
                 if (visits) visits[1]++;
+                if (!(dv <= r2)) continue;
                 if (*cnt < k || key_less(dv, id, hd[k - 1], hid[k - 1]))
                     heap_insert(hd, hid, cnt, k, dv, id);   /* C2: r' = new k-th key */
             }
@@ -488,12 +492,13 @@ static void find_knn(const or_tree *t, const float *q, int32_t k, float *hd, int
     }
 }
 
-/* KNN of m queries (host [m][d]) against the tree: ids/d2 [m][k].
- * visits (optional) [m][2].  nthreads <= 0 uses the OpenMP default. */
-int or_knn(const or_tree *t, const float *q, int64_t m, int32_t k, int32_t *ids, float *d2,
-           int64_t *visits, int32_t nthreads)
+/* KNN of m queries (host [m][d]) against the tree: ids/d2 [m][k], neighbours
+ * within squared radius r2 (+inf: unbounded).  visits (optional) [m][2].
+ * nthreads <= 0 uses the OpenMP default. */
+int or_knn_r(const or_tree *t, const float *q, int64_t m, int32_t k, float r2, int32_t *ids, float *d2,
+             int64_t *visits, int32_t nthreads)
 {
-    if (!t || m < 0 || k < 1 || (m > 0 && (!q || !ids || !d2))) return OR_ERR_INVALID;
+    if (!t || m < 0 || k < 1 || (m > 0 && (!q || !ids || !d2)) || !(r2 >= 0.0f)) return OR_ERR_INVALID;
     if (k > 4096) return OR_ERR_UNSUPPORTED;
     for (int64_t i = 0; i < m * t->d; i++)
         if (!isfinite(q[i])) return OR_ERR_NONFINITE;
@@ -516,7 +521,7 @@ int or_knn(const or_tree *t, const float *q, int64_t m, int32_t k, int32_t *ids,
                 int32_t cnt = 0;
                 int64_t *v = visits ? visits + 2 * i : NULL;
                 if (v) v[0] = v[1] = 0;
-                find_knn(t, q + i * t->d, k, hd, hid, &cnt, v);
+                find_knn(t, q + i * t->d, k, r2, hd, hid, &cnt, v);
                 write_row(hd, hid, cnt, k, ids + i * k, d2 + i * k);
             }
         }
@@ -526,11 +531,18 @@ int or_knn(const or_tree *t, const float *q, int64_t m, int32_t k, int32_t *ids,
     return failed ? OR_ERR_NOMEM : OR_OK;
 }
 
-/* The plain definition: exhaustive search over all n points. */
-int or_brute_knn(const float *pts, int64_t n, int32_t d, const float *q, int64_t m, int32_t k,
-                 int32_t *ids, float *d2, int32_t nthreads)
+int or_knn(const or_tree *t, const float *q, int64_t m, int32_t k, int32_t *ids, float *d2,
+           int64_t *visits, int32_t nthreads)
 {
-    if (!pts || n < 1 || d < 1 || k < 1 || m < 0 || (m > 0 && (!q || !ids || !d2)))
+    return or_knn_r(t, q, m, k, INFINITY, ids, d2, visits, nthreads);
+}
+
+/* The plain definition: exhaustive search over all n points, neighbours
+ * within squared radius r2 (+inf: unbounded). */
+int or_brute_knn_r(const float *pts, int64_t n, int32_t d, const float *q, int64_t m, int32_t k, float r2,
+                   int32_t *ids, float *d2, int32_t nthreads)
+{
+    if (!pts || n < 1 || d < 1 || k < 1 || m < 0 || (m > 0 && (!q || !ids || !d2)) || !(r2 >= 0.0f))
         return OR_ERR_INVALID;
     if (k > 4096) return OR_ERR_UNSUPPORTED;
 #ifdef _OPENMP
@@ -553,6 +565,7 @@ int or_brute_knn(const float *pts, int64_t n, int32_t d, const float *q, int64_t
                 const float *qi = q + i * d;
                 for (int64_t j = 0; j < n; j++) {
                     float dv = sq_dist(qi, pts + j * d, d);
+                    if (!(dv <= r2)) continue;
                     if (cnt < k || key_less(dv, (int32_t)j, hd[k - 1], hid[k - 1]))
                         heap_insert(hd, hid, &cnt, k, dv, (int32_t)j);
                 }
@@ -563,6 +576,12 @@ int or_brute_knn(const float *pts, int64_t n, int32_t d, const float *q, int64_t
         free(hid);
     }
     return failed ? OR_ERR_NOMEM : OR_OK;
+}
+
+int or_brute_knn(const float *pts, int64_t n, int32_t d, const float *q, int64_t m, int32_t k,
+                 int32_t *ids, float *d2, int32_t nthreads)
+{
+    return or_brute_knn_r(pts, n, d, q, m, k, INFINITY, ids, d2, nthreads);
 }
 
 /* Same as or_brute_knn for a subset of query rows: rows[r] indexes q. */

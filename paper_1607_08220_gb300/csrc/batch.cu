@@ -311,6 +311,10 @@ panda_status panda_batch_set_query_params(panda_batch* b, const panda_query_para
         set_error("panda_batch_set_query_params: a batch orders queries by leaf");
         return PANDA_ERR_UNSUPPORTED;
     }
+    if (params && params->bounded) {
+        set_error("panda_batch_set_query_params: a batch answers unbounded queries");
+        return PANDA_ERR_UNSUPPORTED;
+    }
     if (b->exec) {
         // the parameters are baked into the captured graph: wait for every run
         // in flight, drop the graph, and capture again at the next run

@@ -52,6 +52,8 @@ panda_status configure_knn()
         if (st == PANDA_OK) st = configure_knn_variant<DP, kKnnManySets, true>();
         if (st == PANDA_OK) st = configure_knn_variant<DP, kKnnStats, false>();
         if (st == PANDA_OK) st = configure_knn_variant<DP, kKnnStats, true>();
+        if (st == PANDA_OK) st = configure_knn_variant<DP, kKnnRadius, false>();
+        if (st == PANDA_OK) st = configure_knn_variant<DP, kKnnRadius, true>();
         if (st == PANDA_OK) st = fill_multi_blocks<DP, false>();
         if (st == PANDA_OK) st = fill_multi_blocks<DP, true>();
         return st;
@@ -86,7 +88,12 @@ panda_status launch_knn_dp(const KnnArgs& a, cudaStream_t s)
     const long long warps = a.pos_jobs ? a.pos_jobs_cap : (a.m + 31) / 32;
     const long long blocks = (warps + kKnnThreads / 32 - 1) / (kKnnThreads / 32);
     if (blocks <= 0) return PANDA_OK;
-    if (a.stats || a.visits) {
+    if (a.rkey) {
+        if (a.solo)
+            k_knn<DP, kKnnRadius, true><<<(unsigned)blocks, kKnnThreads, heap_bytes, s>>>(a);
+        else
+            k_knn<DP, kKnnRadius, false><<<(unsigned)blocks, kKnnThreads, heap_bytes, s>>>(a);
+    } else if (a.stats || a.visits) {
         if (a.solo)
             k_knn<DP, kKnnStats, true><<<(unsigned)blocks, kKnnThreads, heap_bytes, s>>>(a);
         else

@@ -170,6 +170,32 @@ __global__ void k_bin_jobs(const int* cursor, const int* bsum, int nb, int2* job
     for (int j = 0; j < nj; j++) jobs[base + j] = make_int2(start + 32 * j, min(32, count - 32 * j));
 }
 
+// Key of the search radius: (max_d2 bits, 0xffffffff) -- every point with
+// d2 <= max_d2 has a smaller key (ids < 2^31); 0 when the query is unbounded.
+static unsigned long long radius_key(const panda_query_params* params)
+{
+    if (!params || !params->bounded) return 0ull;
+    unsigned bits;
+    const float r2 = params->max_d2 + 0.0f;   // -0 -> +0
+    memcpy(&bits, &r2, 4);
+    return ((unsigned long long)bits << 32) | 0xffffffffull;
+}
+
+// Radius parameters are valid: unbounded, or max_d2 >= 0 (not NaN).
+static panda_status check_radius(const panda_query_params* params, bool counters, const char* what)
+{
+    if (!params || !params->bounded) return PANDA_OK;
+    if (!(params->max_d2 >= 0.0f)) {
+        set_error("%s: max_d2 must be >= 0", what);
+        return PANDA_ERR_INVALID_ARGUMENT;
+    }
+    if (counters) {
+        set_error("%s: work counters are not kept for radius-bounded queries", what);
+        return PANDA_ERR_UNSUPPORTED;
+    }
+    return PANDA_OK;
+}
+
 template <int DP>
 panda_status launch_knn_dp(const KnnArgs& a, cudaStream_t s);
 
@@ -206,6 +232,10 @@ panda_status knn_query(const panda_tree* t, const float* queries, int64_t m, int
     if (!is_device_ptr(queries) || !is_device_ptr(ids) || !is_device_ptr(d2)) {
         set_error("panda_knn: queries and outputs must be device pointers");
         return PANDA_ERR_INVALID_ARGUMENT;
+    }
+    {
+        const panda_status rs = check_radius(params, visits || stats, "panda_knn");
+        if (rs != PANDA_OK) return rs;
     }
     const int order = params ? params->order : PANDA_ORDER_LEAF;
     if (order < PANDA_ORDER_NONE || order > PANDA_ORDER_LEAF) {
@@ -317,6 +347,7 @@ panda_status knn_query(const panda_tree* t, const float* queries, int64_t m, int
     ka.stats = stats;
     ka.transpose_max = (params && params->transpose_max != 0) ? params->transpose_max : kTransposeMaxDefault;
     ka.solo = solo;
+    ka.rkey = radius_key(params);
     ka.pos_jobs = jobs;
     ka.pos_njobs = njobs;
     ka.pos_jobs_cap = jobs_cap;
@@ -395,6 +426,10 @@ panda_status knn_self(const panda_tree* t, int32_t k, int32_t* ids, float* d2, c
         set_error("panda_knn_self: outputs must be device pointers");
         return PANDA_ERR_INVALID_ARGUMENT;
     }
+    {
+        const panda_status rs = check_radius(params, visits || stats, "panda_knn_self");
+        if (rs != PANDA_OK) return rs;
+    }
     PhaseTimer timer(stream);
     // scratch: error word, job counter, jobs (at most one per leaf plus one per
     // 32 points), the bin histogram (bins of 1,024 positions) and its block sums
@@ -456,6 +491,7 @@ panda_status knn_self(const panda_tree* t, int32_t k, int32_t* ids, float* d2, c
     ka.stats = stats;
     ka.transpose_max = (params && params->transpose_max != 0) ? params->transpose_max : kTransposeMaxDefault;
     ka.solo = (params && params->traversal == PANDA_TRAVERSAL_PER_QUERY) ? 1 : 0;
+    ka.rkey = radius_key(params);
     ka.d = t->d;
     ka.k = k;
     st = launch_knn(ka, t->dp, stream);

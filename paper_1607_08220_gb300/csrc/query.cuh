@@ -98,13 +98,16 @@ struct KnnArgs {
     const int2* pos_jobs;    // warp w takes the positions [x, x + y) of job w (y <= 32):
     const int* pos_njobs;    // one leaf's queries, or a 32-query piece of them
     long long pos_jobs_cap;  // warps launched for the jobs (their number is at most this)
+    unsigned long long rkey; // radius-bounded query (kKnnRadius): key (max_d2 bits, 0xffffffff),
+                             // a point is a neighbour only if its key is below it; 0: unbounded
 };
 
 // Kernel modes: one tree and one query set; one tree and the queries of
 // several requests (per-lane request lookup); many sets from a job queue (a
 // set may span several requests); one tree and one query set with the work
-// counters (visits, stats) compiled in.
-enum KnnMode { kKnnOneSet = 0, kKnnOneTreeReqs = 1, kKnnManySets = 2, kKnnStats = 3 };
+// counters (visits, stats) compiled in; one tree and one query set with a
+// search radius (Algorithm 1's r).
+enum KnnMode { kKnnOneSet = 0, kKnnOneTreeReqs = 1, kKnnManySets = 2, kKnnStats = 3, kKnnRadius = 4 };
 
 constexpr unsigned long long kKeyEmpty = (0x7f800000ull << 32) | 0xffffffffull;
 constexpr int kKnnThreads = 128;
@@ -156,7 +159,7 @@ __device__ __forceinline__ float record_box_d2(const float4* rec, const float (&
 // its own stack of (node, bound) where a child's bound is its box distance,
 // computed at the parent; the far child is pushed only if its bound does not
 // exceed r', the near child last; buckets are scanned point by point.
-template <int DP>
+template <int DP, bool RAD>
 __device__ __forceinline__ void knn_lane_solo(const KnnArgs& a, const KnnSet& S, const float (&q)[DP],
                                               unsigned long long* h, int K, unsigned long long& kth,
                                               int& vnodes, int& vpts)
@@ -213,7 +216,7 @@ __device__ __forceinline__ void knn_lane_solo(const KnnArgs& a, const KnnSet& S,
                     ((unsigned long long)__float_as_uint(acc) << 32) | (unsigned)__float_as_int(pv[DP]);
                 if (key < kth) {
                     heap_replace_root(h, K, key);
-                    kth = h[0];
+                    kth = RAD ? min(h[0], a.rkey) : h[0];
                 }
             }
         } else {
@@ -247,7 +250,7 @@ __device__ __forceinline__ void knn_lane_solo(const KnnArgs& a, const KnnSet& S,
 // compiles the per-query traversal in (taken when S.solo is set); without it
 // the kernel holds the packet traversal alone and keeps its registers.  REQS
 // compiles in the per-lane request lookup of sets that span several requests.
-template <int DP, bool SOLO_OK, bool REQS, bool STATS>
+template <int DP, bool SOLO_OK, bool REQS, bool STATS, bool RAD>
 __device__ __forceinline__ void knn_warp_job(const KnnArgs& a, const KnnSet& S, long long g0, int cnt,
                                              float (*sx)[32], int* sid, unsigned long long* h)
 {
@@ -303,7 +306,7 @@ __device__ __forceinline__ void knn_warp_job(const KnnArgs& a, const KnnSet& S, 
     for (int i = 0; i < K; i++) h[i * kKnnThreads] = kKeyEmpty;
     h[K * kKnnThreads] = 0ull;   // sentinel below the heap
     // k-th best key so far (the heap root); invalid lanes never accept anything
-    unsigned long long kth = valid ? kKeyEmpty : 0ull;
+    unsigned long long kth = valid ? (RAD ? a.rkey : kKeyEmpty) : 0ull;
 
     int vnodes = 0, vpts = 0;
     // diagnostics: inner nodes, leaf chunks, lanes=queries chunks, transposed
@@ -313,7 +316,7 @@ __device__ __forceinline__ void knn_warp_job(const KnnArgs& a, const KnnSet& S, 
     unsigned st[11] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
     const bool stats = STATS && a.stats != nullptr;
     if (SOLO_OK && S.solo) {
-        if (valid) knn_lane_solo<DP>(a, S, q, h, K, kth, vnodes, vpts);
+        if (valid) knn_lane_solo<DP, RAD>(a, S, q, h, K, kth, vnodes, vpts);
     } else {
     int stack[kMaxDepth + 4];
     int sp = 0;
@@ -413,7 +416,7 @@ __device__ __forceinline__ void knn_warp_job(const KnnArgs& a, const KnnSet& S, 
                                 if (stats) st[5]++;
                                 if (key < kth) {
                                     heap_replace_root(h, K, key);
-                                    kth = h[0];
+                                    kth = RAD ? min(h[0], a.rkey) : h[0];
                                     kdl = __uint_as_float((unsigned)(kth >> 32));
                                     if (stats) st[6]++;
                                 }
@@ -462,7 +465,7 @@ __device__ __forceinline__ void knn_warp_job(const KnnArgs& a, const KnnSet& S, 
                         ((unsigned long long)__float_as_uint(acc) << 32) | (unsigned)sid[j];
                     if (key < kth) {
                         heap_replace_root(h, K, key);
-                        kth = h[0];
+                        kth = RAD ? min(h[0], a.rkey) : h[0];
                         if (stats) {
                             st[6]++;
                             if (!lanes_queries) st[10]++;
@@ -579,7 +582,8 @@ __global__ void __launch_bounds__(kKnnThreads, knn_min_blocks(DP, MODE, SOLO)) k
             cnt = jb.y;
         }
         if (g0 >= a.m) return;
-        knn_warp_job<DP, SOLO, MODE == kKnnOneTreeReqs, MODE == kKnnStats>(a, S, g0, cnt, stage_x[warp],
+        knn_warp_job<DP, SOLO, MODE == kKnnOneTreeReqs, MODE == kKnnStats, MODE == kKnnRadius>(
+            a, S, g0, cnt, stage_x[warp],
                                                                            stage_id[warp], h);
         return;
     }
@@ -591,7 +595,7 @@ __global__ void __launch_bounds__(kKnnThreads, knn_min_blocks(DP, MODE, SOLO)) k
         if (j >= a.njobs) break;
         const KnnJob jb = a.jobs[j];
         const KnnSet S = a.sets[jb.set];
-        knn_warp_job<DP, SOLO, true, false>(a, S, jb.pos, 32, stage_x[warp], stage_id[warp], h);
+        knn_warp_job<DP, SOLO, true, false, false>(a, S, jb.pos, 32, stage_x[warp], stage_id[warp], h);
         __syncwarp();
     }
 }

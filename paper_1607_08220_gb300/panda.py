@@ -78,7 +78,7 @@ class PandaError(RuntimeError):
 
 class QueryParams(ctypes.Structure):
     _fields_ = [("order", ctypes.c_int32), ("transpose_max", ctypes.c_int32), ("traversal", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("bounded", ctypes.c_int32), ("max_d2", ctypes.c_float), ("reserved", ctypes.c_int32)]
 
 
 class TreeInfo(ctypes.Structure):
@@ -231,6 +231,15 @@ class TuneResult(ctypes.Structure):
 
 
 ORDER_NAMES = {v: k for k, v in ORDER.items()}
+
+
+def _params(order="leaf", transpose_max=0, traversal="auto", max_d2=None) -> "QueryParams":
+    """Query parameters; max_d2 (squared search radius, Algorithm 1's r^2) bounds
+    the neighbours to d2 <= max_d2 when given."""
+    o = ORDER[order] if isinstance(order, str) else int(order)
+    if max_d2 is None:
+        return QueryParams(o, int(transpose_max), TRAVERSAL[traversal], 0, 0.0, 0)
+    return QueryParams(o, int(transpose_max), TRAVERSAL[traversal], 1, float(max_d2), 0)
 TRAVERSAL_NAMES = {v: k for k, v in TRAVERSAL.items()}
 
 
@@ -424,7 +433,7 @@ def build(points, bucket: int = 32, stream=None, sync: bool = True) -> Tree:
 
 
 def knn(tree: Tree, queries, k: int, order: str = "leaf", stream=None, out=None, transpose_max: int = 0,
-        traversal: str = "auto"):
+        traversal: str = "auto", max_d2=None):
     """Exact KNN (Algorithm 1, corrected) of every query row; enqueued on `stream`.
 
     Returns (ids int32 [m][k], d2 float32 [m][k]) CUDA tensors."""
@@ -437,15 +446,15 @@ def knn(tree: Tree, queries, k: int, order: str = "leaf", stream=None, out=None,
         d2 = torch.empty((m, k), dtype=torch.float32, device=q.device)
     else:
         ids, d2 = out
-    prm = QueryParams(ORDER[order] if isinstance(order, str) else int(order), int(transpose_max),
-                      TRAVERSAL[traversal], 0)
+    prm = _params(order, transpose_max, traversal, max_d2)
     _check(L.panda_knn_async(tree.handle, ctypes.c_void_p(q.data_ptr()), m, int(k),
                              ctypes.c_void_p(ids.data_ptr()), ctypes.c_void_p(d2.data_ptr()),
                              ctypes.byref(prm), _stream_ptr(stream)))
     return ids, d2
 
 
-def knn_self(tree: Tree, k: int, stream=None, out=None, transpose_max: int = 0, traversal: str = "auto"):
+def knn_self(tree: Tree, k: int, stream=None, out=None, transpose_max: int = 0, traversal: str = "auto",
+             max_d2=None):
     """All-points KNN: every point of the tree is a query (row i = input point i).
 
     Enqueued on `stream`; returns (ids int32 [n][k], d2 float32 [n][k]) CUDA tensors."""
@@ -457,7 +466,7 @@ def knn_self(tree: Tree, k: int, stream=None, out=None, transpose_max: int = 0, 
         d2 = torch.empty((n, k), dtype=torch.float32, device="cuda")
     else:
         ids, d2 = out
-    prm = QueryParams(ORDER["leaf"], int(transpose_max), TRAVERSAL[traversal], 0)
+    prm = _params("leaf", transpose_max, traversal, max_d2)
     _check(L.panda_knn_self_async(tree.handle, int(k), ctypes.c_void_p(ids.data_ptr()),
                                   ctypes.c_void_p(d2.data_ptr()), ctypes.byref(prm), _stream_ptr(stream)))
     return ids, d2
@@ -475,7 +484,7 @@ def knn_self_sync(tree: Tree, k: int):
     return ids, d2
 
 
-def knn_self_host(tree: Tree, k: int, stream=None, out: tuple | None = None):
+def knn_self_host(tree: Tree, k: int, stream=None, out: tuple | None = None, max_d2=None):
     """panda_knn_self_host: all-points query into host outputs (copy out inside the call)."""
     L = load()
     n = tree.info()["n"]
@@ -484,7 +493,7 @@ def knn_self_host(tree: Tree, k: int, stream=None, out: tuple | None = None):
         d2 = np.empty((n, k), np.float32)
     else:
         ids, d2 = out
-    prm = QueryParams(ORDER["leaf"], 0, 0, 0)
+    prm = _params("leaf", 0, "auto", max_d2)
     _check(L.panda_knn_self_host(tree.handle, int(k), ids.ctypes.data_as(ctypes.c_void_p),
                                  d2.ctypes.data_as(ctypes.c_void_p), ctypes.byref(prm), _stream_ptr(stream)))
     return ids, d2
@@ -581,7 +590,7 @@ def build_host(points: np.ndarray, bucket: int = 32, stream=None) -> Tree:
 
 
 def knn_host(tree: Tree, queries: np.ndarray, k: int, order: str = "leaf", stream=None,
-             out: tuple | None = None):
+             out: tuple | None = None, max_d2=None):
     """panda_knn_host: host queries and outputs; copies in and out inside the call."""
     L = load()
     q = np.ascontiguousarray(queries, dtype=np.float32)
@@ -591,7 +600,7 @@ def knn_host(tree: Tree, queries: np.ndarray, k: int, order: str = "leaf", strea
         d2 = np.empty((m, k), np.float32)
     else:
         ids, d2 = out
-    prm = QueryParams(ORDER[order], 0, 0, 0)
+    prm = _params(order, 0, "auto", max_d2)
     _check(L.panda_knn_host(tree.handle, q.ctypes.data_as(ctypes.c_void_p), m, int(k),
                             ids.ctypes.data_as(ctypes.c_void_p), d2.ctypes.data_as(ctypes.c_void_p),
                             ctypes.byref(prm), _stream_ptr(stream)))

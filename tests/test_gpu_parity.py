@@ -149,6 +149,65 @@ def test_self_query_parity(P, case):
     assert_same_knn(hi, hd, eids, ed2)
 
 
+def _radius_cases():
+    rng = np.random.default_rng(41)
+    w = workloads.uniform_small()
+    yield "uniform_small", w.points, w.queries, 8, 32, (0.0, 2e-5, 1e-4, 1e-3)
+    lat = workloads.lattice_points(5000, 3, seed=5, side=6)
+    yield "lattice_ties", lat, workloads.lattice_points(333, 3, seed=6, side=6), 20, 16, \
+        (0.0, 2.0 ** -8, 2 * 2.0 ** -8, 2.0 ** -6)
+    dup = np.repeat(rng.random((6, 3), dtype=np.float32), 700, axis=0)
+    yield "heavy_dups", dup, dup[::97], 17, 32, (0.0, 0.01)
+    yield "gauss_d10", rng.standard_normal((20000, 10)).astype(np.float32), \
+        rng.standard_normal((500, 10)).astype(np.float32), 16, 32, (1.0, 4.0)
+
+
+@pytest.mark.parametrize("case", list(_radius_cases()), ids=lambda c: c[0])
+def test_radius_parity(P, case):
+    """Algorithm 1's search radius: only points with d2 <= max_d2, padded with
+    (-1, +inf); equal to the oracle for both traversal shapes, the all-points
+    query and the host variant."""
+    import torch
+    name, pts, q, k, B, radii = case
+    t = P.build(dev(pts), B)
+    ot = oracle.build(pts, B)
+    for r2 in radii:
+        eids, ed2 = oracle.knn(ot, q, k, max_d2=r2)
+        for trav in ("packet", "per_query"):
+            ids, d2 = P.knn(t, dev(q), k, traversal=trav, max_d2=r2)
+            torch.cuda.synchronize()
+            assert_same_knn(ids.cpu().numpy(), d2.cpu().numpy(), eids, ed2)
+        hi, hd = P.knn_host(t, q, k, max_d2=r2)
+        assert_same_knn(hi, hd, eids, ed2)
+        sids, sd2 = oracle.knn(ot, pts, k, max_d2=r2)
+        si, sd = P.knn_self(t, k, max_d2=r2)
+        torch.cuda.synchronize()
+        assert_same_knn(si.cpu().numpy(), sd.cpu().numpy(), sids, sd2)
+
+
+def test_radius_errors(P):
+    import torch
+    pts = np.random.default_rng(0).random((1000, 3), dtype=np.float32)
+    t = P.build(dev(pts), 32)
+    for bad in (-1.0, float("nan")):
+        with pytest.raises(P.PandaError) as e:
+            P.knn(t, dev(pts[:10]), 4, max_d2=bad)
+        assert e.value.status == 1
+    prm = P._params("leaf", 0, "auto", 0.01)
+    ids = torch.empty((10, 4), dtype=torch.int32, device="cuda")
+    d2 = torch.empty((10, 4), dtype=torch.float32, device="cuda")
+    vis = torch.zeros((10, 2), dtype=torch.int32, device="cuda")
+    q = dev(pts[:10])
+    import ctypes
+    st = P.load().panda_knn_visits(t.handle, ctypes.c_void_p(q.data_ptr()), 10, 4, ctypes.c_void_p(ids.data_ptr()),
+                                   ctypes.c_void_p(d2.data_ptr()), ctypes.c_void_p(vis.data_ptr()), None,
+                                   ctypes.byref(prm), None)
+    assert st == 3                                     # work counters: unbounded queries only
+    ok = P.knn(t, dev(pts[:10]), 4, max_d2=0.0)[0]     # the library stays usable
+    torch.cuda.synchronize()
+    assert ok[:, 0].cpu().tolist() == list(range(10))
+
+
 def test_phase_timing_many_levels(P):
     """Phase timing across a build with many level passes (event bookkeeping)."""
     pts = np.random.default_rng(4).random((3_000_000, 3), dtype=np.float32)

@@ -262,3 +262,63 @@ def test_literal_bound_over_prunes():
     true_region_distance = 2.0
     r_prime = 2.2
     assert literal > r_prime > 2.1 > true_region_distance
+
+
+# ------------------------------------------------------------------ radius-bounded KNN (Algorithm 1's r)
+
+
+def _numpy_radius_knn(pts, q, k, r2):
+    """The plain definition written with numpy FP32 elementwise ops (each op
+    rounded, dims in order, no FMA): the k smallest (d2, id) among d2 <= r2."""
+    pts = pts.astype(np.float32)
+    out_i = np.full((q.shape[0], k), -1, np.int32)
+    out_d = np.full((q.shape[0], k), np.inf, np.float32)
+    for r in range(q.shape[0]):
+        diff = (q[r][None, :] - pts).astype(np.float32)
+        sq = (diff * diff).astype(np.float32)
+        d2 = sq[:, 0].copy()
+        for j in range(1, pts.shape[1]):
+            d2 = (d2 + sq[:, j]).astype(np.float32)
+        ok = np.flatnonzero(d2 <= np.float32(r2))
+        order = ok[np.lexsort((ok, d2[ok]))][:k]
+        out_i[r, :order.size] = order
+        out_d[r, :order.size] = d2[order]
+    return out_i, out_d
+
+
+def test_radius_brute_matches_numpy_definition(oracle_mod):
+    rng = np.random.default_rng(31)
+    pts = rng.random((700, 3), dtype=np.float32)
+    q = rng.random((60, 3), dtype=np.float32)
+    for r2 in (0.0, 0.001, 0.01, 0.05, np.inf):
+        bi, bd = oracle_mod.brute_knn(pts, q, 9, max_d2=r2)
+        ni, nd = _numpy_radius_knn(pts, q, 9, r2)
+        assert np.array_equal(bi, ni) and np.array_equal(bd.view(np.uint32), nd.view(np.uint32))
+
+
+def test_radius_tree_matches_brute_with_ties_on_the_radius(oracle_mod):
+    # lattice points: many distances equal the radius exactly (inclusive bound)
+    pts = workloads.lattice_points(3000, 3, seed=8, side=8)
+    q = workloads.lattice_points(200, 3, seed=9, side=8)
+    t = oracle_mod.build(pts, 8)
+    for r2 in (0.0, 2.0 ** -8, 3 * 2.0 ** -8, 2.0 ** -4, 1.0):
+        ti, td = oracle_mod.knn(t, q, 12, max_d2=r2)
+        bi, bd = oracle_mod.brute_knn(pts, q, 12, max_d2=r2)
+        assert np.array_equal(ti, bi) and np.array_equal(td.view(np.uint32), bd.view(np.uint32))
+        assert np.all((td <= np.float32(r2)) | (ti == -1))
+
+
+def test_radius_special_cases(oracle_mod):
+    rng = np.random.default_rng(32)
+    pts = rng.random((500, 2), dtype=np.float32)
+    pts[10] = pts[3]                                   # one exact duplicate pair
+    t = oracle_mod.build(pts, 4)
+    # r2 = 0: a self query finds only itself and its exact duplicates
+    ti, td = oracle_mod.knn(t, pts, 3, max_d2=0.0)
+    assert np.array_equal(ti[:, 0][np.arange(500) != 10], np.arange(500)[np.arange(500) != 10])
+    assert ti[3].tolist()[:2] == [3, 10] and ti[10].tolist()[:2] == [3, 10]
+    assert (ti[:, 2] == -1).all() and np.isinf(td[:, 2]).all()
+    # r2 = +inf is the unbounded query
+    ui, ud = oracle_mod.knn(t, pts, 5)
+    ri, rd = oracle_mod.knn(t, pts, 5, max_d2=np.inf)
+    assert np.array_equal(ui, ri) and np.array_equal(ud.view(np.uint32), rd.view(np.uint32))
