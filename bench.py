@@ -42,7 +42,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=["cosmology_self", "uniform_small", "features_10d", "batched_sets",
-                                           "plasma_serving", "features_10d_served", "features_10d_classify"],
+                                           "plasma_serving", "features_10d_served", "features_10d_classify",
+                                           "cosmology_refit"],
                     default="cosmology_self")
     ap.add_argument("--duration", type=float, default=1.0, help="seconds of the served request stream")
     ap.add_argument("--nsets", type=int, default=512, help="sets of the batched workload")
@@ -763,6 +764,87 @@ def run_served(args):
     return 0
 
 
+def run_refit(args):
+    """Moving particles: per simulation step either refit the tree (panda_refit:
+    new coordinates, same structure) or rebuild it, then the all-points query."""
+    import torch
+
+    import paper_1607_08220_gb300 as P
+    from paper_1607_08220_gb300 import build_ext, workloads
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    build_ext.build()
+    P.load()
+    w = workloads.cosmology_self(n=args.n) if args.n else workloads.cosmology_self()
+    n, k, B = w.points.shape[0], w.k, w.bucket
+    nsteps = max(args.steps, 2)
+    # velocities: a smooth flow (neighbours move together, as particles of one
+    # halo do) of up to 0.1 x the mean inter-particle spacing per step, plus a
+    # random part of 0.01 x the spacing
+    rng = np.random.default_rng(7)
+    spacing = float(n) ** (-1.0 / 3.0)
+    x = w.points.astype(np.float64)
+    ph = rng.uniform(0, 2 * np.pi, 3)
+    flow = np.stack([np.sin(2 * np.pi * x[:, 1] + ph[0]), np.sin(2 * np.pi * x[:, 2] + ph[1]),
+                     np.sin(2 * np.pi * x[:, 0] + ph[2])], axis=1)
+    v = 0.1 * spacing * flow + 0.01 * spacing * rng.standard_normal(w.points.shape)
+    vel = torch.from_numpy(v.astype(np.float32)).cuda()
+    p0 = torch.from_numpy(w.points).cuda()
+    ids = torch.empty((n, k), dtype=torch.int32, device="cuda")
+    d2 = torch.empty((n, k), dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def run(mode):
+        pts = p0.clone()
+        t = P.build(pts, B)
+        P.knn_self(t, k, out=(ids, d2))
+        torch.cuda.synchronize()
+        per = []
+        for _ in range(nsteps):
+            pts.add_(vel)                      # the simulation's move (not timed)
+            torch.cuda.synchronize()
+            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            e0.record(stream)
+            if mode == "refit":
+                P.refit(t, pts)
+            else:
+                t.free()
+                t = P.build(pts, B)
+            e1.record(stream)
+            P.knn_self(t, k, out=(ids, d2))
+            e2.record(stream)
+            torch.cuda.synchronize()
+            per.append((e0.elapsed_time(e1), e1.elapsed_time(e2)))
+        res = (ids.clone(), d2.clone())
+        t.free()
+        return per, res
+
+    for _ in range(max(1, args.warmup)):
+        run("refit")
+    clocks = ClockSampler(os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0].strip())
+    clocks.start()
+    rf, rres = run("refit")
+    rb, bres = run("rebuild")
+    clk = clocks.stop()
+    same = torch.equal(rres[0], bres[0]) and torch.equal(rres[1].view(torch.int32), bres[1].view(torch.int32))
+    refit_ms = sum(a + b for a, b in rf) / nsteps
+    rebuild_ms = sum(a + b for a, b in rb) / nsteps
+    line = {"metric": METRIC + " [moving particles: refit vs rebuild]", "value": n / (refit_ms / 1e3),
+            "unit": UNIT, "n_gpus": 1, "steps": nsteps, "warmup": max(1, args.warmup), "ms_per_step": refit_ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": f"cosmology_refit: n={n} k={k} B={B}, every point moves by a fixed velocity "
+                                   f"per step (a smooth flow of up to 0.1 x the mean spacing plus a random "
+                                   f"0.01 x the spacing), all-points query each step",
+                       "l2": "inputs larger than L2"},
+            "clocks": clk,
+            "refit": {"ms_per_step": refit_ms, "per_step_refit_query_ms": [[round(a, 3), round(b, 3)] for a, b in rf]},
+            "rebuild": {"ms_per_step": rebuild_ms, "value": n / (rebuild_ms / 1e3),
+                        "per_step_build_query_ms": [[round(a, 3), round(b, 3)] for a, b in rb]},
+            "identical_final_results": bool(same)}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -771,6 +853,8 @@ def main():
         return run_batched(args)
     if args.workload in ("plasma_serving", "features_10d_served"):
         return run_served(args)
+    if args.workload == "cosmology_refit":
+        return run_refit(args)
     return run_ours(args)
 
 

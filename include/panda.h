@@ -159,6 +159,17 @@ panda_status panda_knn_self_async(const panda_tree* tree, int32_t k, int32_t* ou
 panda_status panda_knn_self_host(const panda_tree* tree, int32_t k, int32_t* out_ids, float* out_d2,
                                  const panda_query_params* params, void* stream);
 
+/* ---- refit: particles moved (Sec. II: the tree is rebuilt every few steps of a
+ * simulation; in between it can be refitted) ---------------------------------
+ * points: device [n][d] FP32, the new coordinates of the tree's points in the
+ * original id order.  Every point keeps its leaf; leaf boxes become the exact
+ * boxes of the new coordinates and inner boxes the union of their children's,
+ * so later queries are exact for the new positions (they slow down as the
+ * split planes drift away from the points).  Synchronises `stream`; a
+ * non-finite coordinate returns PANDA_ERR_NONFINITE_INPUT and changes nothing.
+ * Trees of the batched or served forms are not refitted. */
+panda_status panda_refit(panda_tree* tree, const float* points, void* stream);
+
 /* ---- prediction from a KNN result (Sec. I: majority vote for classification,
  * average for regression) ----------------------------------------------------
  * ids: device [m][k] int32 as written by a query on a tree of n points (entries

@@ -34,6 +34,7 @@ SIGNATURES = {
     "panda_knn_host": ([_P, _P, _I64, _I32, _P, _P, _P, _P], ctypes.c_int),
     "panda_knn_self": ([_P, _I32, _P, _P], ctypes.c_int),
     "panda_knn_vote": ([_P, _I64, _I32, _P, _I64, _P, _P], ctypes.c_int),
+    "panda_refit": ([_P, _P, _P], ctypes.c_int),
     "panda_knn_mean": ([_P, _I64, _I32, _P, _I64, _P, _P], ctypes.c_int),
     "panda_knn_self_async": ([_P, _I32, _P, _P, _P, _P], ctypes.c_int),
     "panda_knn_self_host": ([_P, _I32, _P, _P, _P, _P], ctypes.c_int),
@@ -497,6 +498,14 @@ def knn_self_host(tree: Tree, k: int, stream=None, out: tuple | None = None, max
     _check(L.panda_knn_self_host(tree.handle, int(k), ids.ctypes.data_as(ctypes.c_void_p),
                                  d2.ctypes.data_as(ctypes.c_void_p), ctypes.byref(prm), _stream_ptr(stream)))
     return ids, d2
+
+
+def refit(tree: Tree, points, stream=None):
+    """Move the tree's points to new coordinates (CUDA float32 [n][d], original
+    id order) and make every box tight again; the structure is kept."""
+    L = load()
+    pts = _as_device_points(points, "points")
+    _check(L.panda_refit(tree.handle, ctypes.c_void_p(pts.data_ptr()), _stream_ptr(stream)))
 
 
 def knn_vote(ids, labels, stream=None, out=None):

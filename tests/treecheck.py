@@ -187,3 +187,25 @@ def assert_same_tree(a: dict, b: dict):
     assert np.array_equal(np.asarray(a["split"])[inner], np.asarray(b["split"])[inner]), "split"
     assert np.array_equal(a["lo"], b["lo"]) and np.array_equal(a["hi"], b["hi"]), "boxes"
     assert np.array_equal(np.asarray(a["perm"]), np.asarray(b["perm"])), "leaf order"
+
+
+def check_boxes(t: dict, points: np.ndarray):
+    """Boxes of a tree whose points moved after the build (a refit): the leaf
+    order is still a permutation, every leaf box is the exact box of its
+    points, every inner box the union of its children's."""
+    pts = np.asarray(points, np.float32)
+    n = pts.shape[0]
+    perm = np.asarray(t["perm"], np.int64)
+    assert perm.shape == (n,) and np.all(np.bincount(perm, minlength=n) == 1)
+    P = pts[perm]
+    leaf = np.asarray(t["leaf"], bool)
+    start = np.asarray(t["start"])
+    lv = np.flatnonzero(leaf)
+    ls = np.sort(start[lv])
+    order = lv[np.argsort(start[lv])]
+    assert np.array_equal(t["lo"][order], np.minimum.reduceat(P, ls, axis=0)), "leaf box lo not tight"
+    assert np.array_equal(t["hi"][order], np.maximum.reduceat(P, ls, axis=0)), "leaf box hi not tight"
+    inner = np.flatnonzero(~leaf)
+    l, r = np.asarray(t["left"])[inner], np.asarray(t["right"])[inner]
+    assert np.array_equal(t["lo"][inner], np.minimum(t["lo"][l], t["lo"][r]))
+    assert np.array_equal(t["hi"][inner], np.maximum(t["hi"][l], t["hi"][r]))
