@@ -49,9 +49,21 @@ def _digest(extra: list[str]) -> str:
 
 
 def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None) -> str:
-    """Build (if the sources changed) and return the library path."""
+    """Build (if the sources changed) and return the library path.  Processes
+    that build at once (ranks of one job) take turns on a lock file; the
+    later ones find the library current."""
+    import fcntl
     extra = list(extra or [])
     os.makedirs(OUT_DIR, exist_ok=True)
+    with open(os.path.join(OUT_DIR, "build.lock"), "w") as lock:
+        fcntl.flock(lock, fcntl.LOCK_EX)
+        try:
+            return _build_locked(force, verbose, extra)
+        finally:
+            fcntl.flock(lock, fcntl.LOCK_UN)
+
+
+def _build_locked(force: bool, verbose: bool, extra: list[str]) -> str:
     stamp = os.path.join(OUT_DIR, "libpanda.sha1")
     dig = _digest(extra)
     if not force and os.path.exists(LIB) and os.path.exists(stamp):
