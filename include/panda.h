@@ -309,6 +309,15 @@ panda_status panda_tune_lookup(int32_t d, int64_t n, int32_t k, int64_t m_total,
  * bits in float slot dp, zero padding to a multiple of 4 floats. */
 panda_status panda_tree_get_info(const panda_tree* tree, panda_tree_info* info);
 panda_status panda_tree_copy(const panda_tree* tree, float* host_nodes, float* host_points);
+/* Checkpoint: panda_tree_save writes the tree (header, root box, node table,
+ * packed points) to the file at `path`; panda_tree_load reads one back onto
+ * the current device as a new tree (free it with panda_free).  Loading checks
+ * the header, that the stored ids are a permutation of 0..n-1 and that every
+ * node record stays inside the tables (PANDA_ERR_INVALID_ARGUMENT otherwise).
+ * Queries on a loaded tree return what they return on the saved one.  The
+ * paper has no counterpart: it rebuilds trees. */
+panda_status panda_tree_save(const panda_tree* tree, const char* path);
+panda_status panda_tree_load(const char* path, panda_tree** out);
 
 /* ---- diagnostics --------------------------------------------------------------
  * Phase timing: when enabled, the library records CUDA events on the launching

@@ -6,10 +6,10 @@ The compute path is the CUDA library ``_lib/libpanda.so`` behind the C ABI in
 with :func:`paper_1607_08220_gb300.build_ext.build`.
 """
 from .panda import (Batch, PandaError, Server, Tree, build, build_host, kernel_launches, knn, knn_host,
-                    knn_mean, knn_self, knn_self_host, knn_self_sync, knn_sync, knn_visits, knn_vote, load, refit,
+                    knn_mean, knn_self, knn_self_host, knn_self_sync, knn_sync, knn_visits, knn_vote, load, load_tree, refit, save,
                     phase_times,
                     set_phase_timing, tune, tune_lookup, version)
 
 __all__ = ["Batch", "PandaError", "Server", "Tree", "build", "build_host", "knn", "knn_host", "knn_self",
-           "knn_self_host", "knn_self_sync", "knn_sync", "knn_visits", "knn_vote", "knn_mean", "load", "refit", "phase_times",
+           "knn_self_host", "knn_self_sync", "knn_sync", "knn_visits", "knn_vote", "knn_mean", "load", "load_tree", "refit", "save", "phase_times",
            "set_phase_timing", "kernel_launches", "tune", "tune_lookup", "version"]

@@ -24,7 +24,7 @@ OUT_DIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(OUT_DIR, "libpanda.so")
 
 SOURCES = ["api.cu", "build.cu", "query.cu", "knn_lo.cu", "knn_hi.cu", "noalloc.cu", "batch.cu", "serve.cu", "tune.cu",
-           "predict.cu", "refit.cu"]
+           "predict.cu", "refit.cu", "persist.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--fmad=false", "-Xptxas", "--fmad=false",
               "-Xcompiler", "-fPIC", "-Xcompiler", "-O2", "-I", INCLUDE, "-I", CSRC]

@@ -35,6 +35,8 @@ SIGNATURES = {
     "panda_knn_self": ([_P, _I32, _P, _P], ctypes.c_int),
     "panda_knn_vote": ([_P, _I64, _I32, _P, _I64, _P, _P], ctypes.c_int),
     "panda_refit": ([_P, _P, _P], ctypes.c_int),
+    "panda_tree_save": ([_P, ctypes.c_char_p], ctypes.c_int),
+    "panda_tree_load": ([ctypes.c_char_p, _P], ctypes.c_int),
     "panda_knn_mean": ([_P, _I64, _I32, _P, _I64, _P, _P], ctypes.c_int),
     "panda_knn_self_async": ([_P, _I32, _P, _P, _P, _P], ctypes.c_int),
     "panda_knn_self_host": ([_P, _I32, _P, _P, _P, _P], ctypes.c_int),
@@ -498,6 +500,18 @@ def knn_self_host(tree: Tree, k: int, stream=None, out: tuple | None = None, max
     _check(L.panda_knn_self_host(tree.handle, int(k), ids.ctypes.data_as(ctypes.c_void_p),
                                  d2.ctypes.data_as(ctypes.c_void_p), ctypes.byref(prm), _stream_ptr(stream)))
     return ids, d2
+
+
+def save(tree: Tree, path: str):
+    """Write the tree to a file (panda_tree_save)."""
+    _check(load().panda_tree_save(tree.handle, os.fsencode(path)))
+
+
+def load_tree(path: str) -> Tree:
+    """Read a saved tree onto the current device (panda_tree_load)."""
+    h = ctypes.c_void_p()
+    _check(load().panda_tree_load(os.fsencode(path), ctypes.byref(h)))
+    return Tree(h)
 
 
 def refit(tree: Tree, points, stream=None):
