@@ -5,7 +5,10 @@
 // same nodes, queries are first grouped by a spatial key with one counting
 // sort: either the leaf bucket the query falls into (descending the tree by
 // its split planes) or a 30-bit Morton code over the tree's root box.  The
-// order only changes which queries share a warp, never a result.
+// order only changes which queries share a warp, never a result.  Dense
+// leaf-ordered sets (m >= n/2) then hand each warp one bin's queries (a job
+// list), and the all-points query (knn_self) takes the tree's own packed
+// points, one leaf per warp, with no ordering pass at all.
 #include <math.h>
 #include <string.h>
 

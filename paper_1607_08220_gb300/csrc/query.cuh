@@ -1,7 +1,10 @@
 // query.cuh -- exact KNN traversal kernel (Algorithm 1, corrected) for sm_103a.
 //
-// One warp serves 32 queries (one per lane) that were grouped by spatial key,
-// so they traverse nearly the same nodes.  The warp walks one shared stack
+// One warp serves up to 32 queries (one per lane) that were grouped by spatial
+// key, so they traverse nearly the same nodes: 32 consecutive queries in leaf
+// or Morton order, or -- for the all-points query and dense leaf-ordered
+// query sets -- the queries of one leaf (a job list), so that no packet
+// straddles two leaves.  The warp walks one shared stack
 // (Algorithm 1's S): at every popped node each lane computes its own bound,
 // the squared distance from its query to the node's tight box, and the node
 // is skipped only when every lane's bound is strictly greater than its current
@@ -28,8 +31,8 @@
 // k-th distance; they enter with the exact key (d2 bits << 32 | id) into the
 // lane's heap H of the k best keys: a max-heap in shared memory (interleaved
 // by lane, so the lanes of a warp hit distinct banks), whose root is the
-// radius r' (correction C2).  At the end the heap is emptied in order into
-// the output row.
+// radius r' (correction C2; with a search radius r, r' never exceeds r^2).
+// At the end the heap is emptied in order into the output row.
 #pragma once
 
 #include "common.cuh"
