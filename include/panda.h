@@ -158,6 +158,14 @@ panda_status panda_knn_self_async(const panda_tree* tree, int32_t k, int32_t* ou
                                   const panda_query_params* params, void* stream);
 panda_status panda_knn_self_host(const panda_tree* tree, int32_t k, int32_t* out_ids, float* out_d2,
                                  const panda_query_params* params, void* stream);
+/* Enqueue-only host variant: the copy into out_ids / out_d2 (pinned host
+ * memory, or the copy blocks) is queued on `stream` and the call returns;
+ * the results are there once the stream has passed it.  Queries of the next
+ * batch can then run on another stream while this one's results travel.
+ * Device-side consistency checks are not read back (the blocking variants
+ * report them). */
+panda_status panda_knn_self_host_async(const panda_tree* tree, int32_t k, int32_t* out_ids, float* out_d2,
+                                       const panda_query_params* params, void* stream);
 
 /* ---- refit: particles moved (Sec. II: the tree is rebuilt every few steps of a
  * simulation; in between it can be refitted) ---------------------------------
@@ -200,6 +208,11 @@ panda_status panda_knn_noalloc(const panda_tree* tree, const float* queries, int
 
 /* Releases the tree's device memory (NULL-safe). */
 void panda_free(panda_tree* tree);
+/* Stream-ordered free: the tree's device memory returns to the pool once the
+ * work queued on `stream` before the call (queries of this tree on other
+ * streams must be ordered before it by the caller) has run; the handle is
+ * gone at once.  Trees read by panda_tree_load are freed as by panda_free. */
+void panda_free_async(panda_tree* tree, void* stream);
 
 /* ---- batched form: many independent point sets, Sec. III-B (query batching) ---
  * A batch owns device buffers for nsets sets of fixed sizes: all points

@@ -334,8 +334,9 @@ panda_status panda_knn_self(const panda_tree* tree, int32_t k, int32_t* out_ids,
     return s;
 }
 
-panda_status panda_knn_self_host(const panda_tree* tree, int32_t k, int32_t* out_ids, float* out_d2,
-                                 const panda_query_params* params, void* stream)
+// Shared by the blocking and the enqueue-only host variants of the all-points query.
+static panda_status knn_self_host_impl(const panda_tree* tree, int32_t k, int32_t* out_ids, float* out_d2,
+                                       const panda_query_params* params, void* stream, bool wait)
 {
     clear_error();
     if (!tree || k < 1 || !out_ids || !out_d2) {
@@ -354,7 +355,8 @@ panda_status panda_knn_self_host(const panda_tree* tree, int32_t k, int32_t* out
     unsigned herr = 0;
     if (st == PANDA_OK) {
         try {
-            st = knn_self(tree, k, static_cast<int32_t*>(di), static_cast<float*>(dd), params, s, &herr);
+            st = knn_self(tree, k, static_cast<int32_t*>(di), static_cast<float*>(dd), params, s,
+                          wait ? &herr : nullptr);
         } catch (...) {
             st = PANDA_ERR_OUT_OF_MEMORY;
         }
@@ -362,7 +364,7 @@ panda_status panda_knn_self_host(const panda_tree* tree, int32_t k, int32_t* out
     if (st == PANDA_OK) {
         cudaError_t e = cudaMemcpyAsync(out_ids, di, ob, cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaMemcpyAsync(out_d2, dd, ob, cudaMemcpyDeviceToHost, s);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e == cudaSuccess && wait) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) st = cuda_fail(e, "panda_knn_self_host copy out");
     }
     ws_free(di, s);
@@ -372,6 +374,18 @@ panda_status panda_knn_self_host(const panda_tree* tree, int32_t k, int32_t* out
         return PANDA_ERR_CUDA;
     }
     return st;
+}
+
+panda_status panda_knn_self_host(const panda_tree* tree, int32_t k, int32_t* out_ids, float* out_d2,
+                                 const panda_query_params* params, void* stream)
+{
+    return knn_self_host_impl(tree, k, out_ids, out_d2, params, stream, true);
+}
+
+panda_status panda_knn_self_host_async(const panda_tree* tree, int32_t k, int32_t* out_ids, float* out_d2,
+                                       const panda_query_params* params, void* stream)
+{
+    return knn_self_host_impl(tree, k, out_ids, out_d2, params, stream, false);
 }
 
 panda_status panda_knn_host(const panda_tree* tree, const float* queries, int64_t m, int32_t k, int32_t* out_ids,
@@ -458,6 +472,24 @@ void panda_free(panda_tree* tree)
     cudaDeviceSynchronize();
     if (tree->nodes) cudaFree(tree->nodes);
     if (tree->points) cudaFree(tree->points);
+    cudaGetLastError();
+    if (cur != tree->device) cudaSetDevice(cur);
+    delete tree;
+}
+
+void panda_free_async(panda_tree* tree, void* stream)
+{
+    if (!tree) return;
+    if (!tree->pooled) {   // not from the stream-ordered pool: the blocking free
+        panda_free(tree);
+        return;
+    }
+    int cur = 0;
+    cudaGetDevice(&cur);
+    if (cur != tree->device) cudaSetDevice(tree->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (tree->nodes) cudaFreeAsync(tree->nodes, s);
+    if (tree->points) cudaFreeAsync(tree->points, s);
     cudaGetLastError();
     if (cur != tree->device) cudaSetDevice(cur);
     delete tree;

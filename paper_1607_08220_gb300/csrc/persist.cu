@@ -129,6 +129,7 @@ panda_status panda_tree_load(const char* path, panda_tree** out)
     }
     panda_tree* t = new panda_tree();
     cudaGetDevice(&t->device);
+    t->pooled = false;
     t->n = n;
     t->d = (int32_t)d;
     t->dp = (int32_t)dp;

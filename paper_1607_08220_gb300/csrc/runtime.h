@@ -26,6 +26,7 @@ struct panda_tree {
     int64_t node_slots = 0;   // records in use in the node table (holes included)
     int32_t depth = 0;
     float root_lo[16] = {0}, root_hi[16] = {0};
+    bool pooled = true;       // nodes/points from the stream-ordered pool (cudaMallocAsync)
 };
 
 namespace panda {

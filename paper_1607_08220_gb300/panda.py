@@ -40,6 +40,8 @@ SIGNATURES = {
     "panda_knn_mean": ([_P, _I64, _I32, _P, _I64, _P, _P], ctypes.c_int),
     "panda_knn_self_async": ([_P, _I32, _P, _P, _P, _P], ctypes.c_int),
     "panda_knn_self_host": ([_P, _I32, _P, _P, _P, _P], ctypes.c_int),
+    "panda_knn_self_host_async": ([_P, _I32, _P, _P, _P, _P], ctypes.c_int),
+    "panda_free_async": ([_P, _P], None),
     "panda_knn_visits": ([_P, _P, _I64, _I32, _P, _P, _P, _P, _P, _P], ctypes.c_int),
     "panda_knn_noalloc": ([_P, _P, _I64, _I32, _P, _P, _P], ctypes.c_int),
     "panda_batch_create": ([_P, _I32, _I32, _I32, ctypes.POINTER(_P)], ctypes.c_int),
@@ -147,9 +149,13 @@ class Tree:
         _check(_lib.panda_tree_get_info(self._h, ctypes.byref(inf)))
         return {f: getattr(inf, f) for f, _ in TreeInfo._fields_}
 
-    def free(self):
+    def free(self, stream=None):
+        """Release the device memory (stream given: in that stream's order)."""
         if self._h:
-            _lib.panda_free(self._h)
+            if stream is None:
+                _lib.panda_free(self._h)
+            else:
+                _lib.panda_free_async(self._h, _stream_ptr(stream))
             self._h = None
 
     def __del__(self):
@@ -487,8 +493,10 @@ def knn_self_sync(tree: Tree, k: int):
     return ids, d2
 
 
-def knn_self_host(tree: Tree, k: int, stream=None, out: tuple | None = None, max_d2=None):
-    """panda_knn_self_host: all-points query into host outputs (copy out inside the call)."""
+def knn_self_host(tree: Tree, k: int, stream=None, out: tuple | None = None, max_d2=None, wait: bool = True):
+    """panda_knn_self_host: all-points query into host outputs (copy out inside
+    the call).  wait=False: panda_knn_self_host_async -- the copy is only
+    queued on `stream` (pass pinned outputs and synchronise the stream)."""
     L = load()
     n = tree.info()["n"]
     if out is None:
@@ -497,8 +505,9 @@ def knn_self_host(tree: Tree, k: int, stream=None, out: tuple | None = None, max
     else:
         ids, d2 = out
     prm = _params("leaf", 0, "auto", max_d2)
-    _check(L.panda_knn_self_host(tree.handle, int(k), ids.ctypes.data_as(ctypes.c_void_p),
-                                 d2.ctypes.data_as(ctypes.c_void_p), ctypes.byref(prm), _stream_ptr(stream)))
+    fn = L.panda_knn_self_host if wait else L.panda_knn_self_host_async
+    _check(fn(tree.handle, int(k), ids.ctypes.data_as(ctypes.c_void_p), d2.ctypes.data_as(ctypes.c_void_p),
+              ctypes.byref(prm), _stream_ptr(stream)))
     return ids, d2
 
 

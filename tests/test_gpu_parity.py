@@ -208,6 +208,28 @@ def test_radius_errors(P):
     assert ok[:, 0].cpu().tolist() == list(range(10))
 
 
+def test_self_host_async_pipelined(P):
+    """Enqueue-only host results and stream-ordered frees, two steps in flight on
+    two streams: every step's host results equal the blocking call's."""
+    import torch
+    pts = workloads.cosmology_points(120_000, seed=44, halos=20)
+    pn = torch.from_numpy(pts).pin_memory().numpy()
+    t = P.build_host(pn, 32)
+    want_i, want_d = P.knn_self_host(t, 8)
+    t.free()
+    sts = [torch.cuda.Stream(), torch.cuda.Stream()]
+    outs = [(torch.empty((pts.shape[0], 8), dtype=torch.int32).pin_memory().numpy(),
+             torch.empty((pts.shape[0], 8), dtype=torch.float32).pin_memory().numpy()) for _ in range(4)]
+    for i in range(4):
+        s = sts[i % 2]
+        tt = P.build_host(pn, 32, stream=s)
+        P.knn_self_host(tt, 8, stream=s, out=outs[i], wait=False)
+        tt.free(stream=s)
+    torch.cuda.synchronize()
+    for oi, od in outs:
+        assert_same_knn(oi, od, want_i, want_d)
+
+
 def test_phase_timing_many_levels(P):
     """Phase timing across a build with many level passes (event bookkeeping)."""
     pts = np.random.default_rng(4).random((3_000_000, 3), dtype=np.float32)
