@@ -426,40 +426,6 @@ def run_ours(args):
                "h2d_bytes_per_step": int(w.points.nbytes + (0 if use_self else w.queries.nbytes)),
                "d2h_bytes_per_step": int(m * k * 8), "ms_per_step": e_ms / args.steps,
                "path": "blocking calls, one step after the other"}
-        if use_self:
-            # two steps in flight on two streams: a step's results travel to the
-            # host while the next step builds and queries (enqueue-only host
-            # variant + stream-ordered free); every step's copies stay inside
-            # the timed region, which ends when the last result is on the host
-            outs2 = [on, (torch.empty((m, k), dtype=torch.int32).pin_memory().numpy(),
-                          torch.empty((m, k), dtype=torch.float32).pin_memory().numpy())]
-            sts = [torch.cuda.Stream(), torch.cuda.Stream()]
-
-            def pipelined(steps):
-                for i in range(steps):
-                    s = sts[i % 2]
-                    t = P.build_host(pn, B, stream=s)
-                    P.knn_self_host(t, k, stream=s, out=outs2[i % 2], wait=False)
-                    t.free(stream=s)
-
-            pipelined(2)
-            torch.cuda.synchronize()
-            barrier()
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            pipelined(args.steps)
-            torch.cuda.synchronize()
-            p_ms = max_over_ranks((time.perf_counter() - t0) * 1e3, world, "cuda")
-            last = outs2[(args.steps - 1) % 2]
-            same = bool(np.array_equal(last[0], ids.cpu().numpy()) and
-                        np.array_equal(last[1].view(np.int32), d2.cpu().numpy().view(np.int32)))
-            e2e_seq = e2e
-            e2e = {"value": whole_job_rate(m * args.steps, world, p_ms / 1e3), "unit": UNIT,
-                   "h2d_bytes_per_step": e2e_seq["h2d_bytes_per_step"],
-                   "d2h_bytes_per_step": e2e_seq["d2h_bytes_per_step"], "ms_per_step": p_ms / args.steps,
-                   "path": "panda_build_host + panda_knn_self_host_async + panda_free_async, two steps in "
-                           "flight on two streams (host wall clock)",
-                   "identical_to_device_results": same, "sequential": e2e_seq}
 
     # ---- roofline of the dominant kernel (outside the timed region: work counts)
     peaks, peak_src = load_peaks()

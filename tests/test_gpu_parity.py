@@ -218,8 +218,9 @@ def test_self_host_async_pipelined(P):
     want_i, want_d = P.knn_self_host(t, 8)
     t.free()
     sts = [torch.cuda.Stream(), torch.cuda.Stream()]
-    outs = [(torch.empty((pts.shape[0], 8), dtype=torch.int32).pin_memory().numpy(),
-             torch.empty((pts.shape[0], 8), dtype=torch.float32).pin_memory().numpy()) for _ in range(4)]
+    keep = [(torch.empty((pts.shape[0], 8), dtype=torch.int32).pin_memory(),
+             torch.empty((pts.shape[0], 8), dtype=torch.float32).pin_memory()) for _ in range(4)]
+    outs = [(a.numpy(), b.numpy()) for a, b in keep]     # views of the pinned tensors kept alive above
     for i in range(4):
         s = sts[i % 2]
         tt = P.build_host(pn, 32, stream=s)
