@@ -61,3 +61,31 @@ def test_status_strings_and_argument_checks(lib):
     assert b"invalid" in L.panda_last_error() or b"unsupported" in L.panda_last_error()
     assert L.panda_knn(None, None, 0, 5, None, None) == 1
     L.panda_free(None)
+
+
+def test_struct_layouts_match_the_binding(tmp_path):
+    """Every struct the binding passes by pointer has the C layout: size and
+    field offsets from a C program compiled against include/panda.h."""
+    from paper_1607_08220_gb300 import panda
+    structs = {"panda_query_params": panda.QueryParams, "panda_tree_info": panda.TreeInfo,
+               "panda_set_desc": panda.SetDesc, "panda_tune_result": panda.TuneResult}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "panda.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in py._fields_:
+            lines.append(f'printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(src)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    got = {}
+    for line in out:
+        if line:
+            cname, field, val = line.split()
+            got[(cname, field)] = int(val)
+    for cname, py in structs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for fname, _ in py._fields_:
+            assert got[(cname, fname)] == getattr(py, fname).offset, (cname, fname)
