@@ -238,7 +238,9 @@ __global__ void k_check_levels(BuildArgs a, int L)
 
 // One block per active node: sample, per-dimension variance, split dimension,
 // bitonic sort of the sample along it.
-__global__ void k_sample(BuildArgs a, int L)
+constexpr int kSampleThreads = 256;   // k_sample's block (8 warps over 1024 samples)
+
+__global__ void __launch_bounds__(kSampleThreads) k_sample(BuildArgs a, int L)
 {
     extern __shared__ float S[];   // [d][kSamples]
     __shared__ float var[kMaxDim];
@@ -283,10 +285,17 @@ __global__ void k_sample(BuildArgs a, int L)
     __syncthreads();
     const int dm = sdim;
     if (!(var[dm] > 0.0f)) return;
+    // Bitonic sort.  Warp w takes the compare-exchange pairs kPairsPerWarp * w
+    // onwards, which touch only its own 2 * kPairsPerWarp elements while the
+    // stride is at most kPairsPerWarp: between two such stages a warp barrier
+    // is enough, around the wider ones the block waits.
+    constexpr int kPairsPerWarp = kSamples / 2 / (kSampleThreads / 32);
     float* v = S + dm * kSamples;
     for (int size = 2; size <= kSamples; size <<= 1) {
         for (int stride = size >> 1; stride > 0; stride >>= 1) {
-            for (int t = threadIdx.x; t < kSamples / 2; t += blockDim.x) {
+#pragma unroll
+            for (int r = 0; r < kPairsPerWarp / 32; r++) {
+                const int t = warp * kPairsPerWarp + 32 * r + lane;
                 int i = 2 * t - (t & (stride - 1));
                 int j = i + stride;
                 bool up = (i & size) == 0;
@@ -296,7 +305,9 @@ __global__ void k_sample(BuildArgs a, int L)
                     v[j] = x;
                 }
             }
-            __syncthreads();
+            const int next = stride > 1 ? stride >> 1 : (size < kSamples ? size : 2 * kSamples);
+            if (stride <= kPairsPerWarp && next <= kPairsPerWarp) __syncwarp();
+            else __syncthreads();
         }
     }
     float* out = a.vs + (long long)ai * kSamples;
@@ -1281,7 +1292,7 @@ panda_status enqueue_level(BuildState& S, int L, cudaStream_t stream, PhaseTimer
                                                      : (1LL << 30), pl.act_cap);
     const int tcap = (int)std::min<long long>(pl.tile_cap, (long long)a.n / kTile + 2LL * acap + 2);
     timer.begin("level.sample");
-    k_sample<<<acap, 256, d * kSamples * 4, stream>>>(a, L);
+    k_sample<<<acap, kSampleThreads, d * kSamples * 4, stream>>>(a, L);
     PANDA_LAUNCHED("k_sample");
     timer.begin("level.hist");
     k_hist<<<tcap, 256, 0, stream>>>(a, L);
