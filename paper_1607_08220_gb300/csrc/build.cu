@@ -123,27 +123,36 @@ __device__ int block_excl_scan(int v, int* sh /*[33]*/, int* total)
 
 // Tiles of the active list `x` (count A): node a covers [start, start+count),
 // cut at absolute multiples of kTile so that interior tiles are aligned.
+constexpr int kPlanPer = 4;   // consecutive active nodes per thread in one pass of the child plan
+
 __device__ void block_plan_tiles(BuildArgs& a, int x, int A)
 {
     __shared__ int sh[33];
     __shared__ int base;
     if (threadIdx.x == 0) base = 0;
     __syncthreads();
-    for (int c = 0; c < A; c += blockDim.x) {
-        int ai = c + threadIdx.x;
-        int nt = 0;
-        Active nd;
-        if (ai < A) {
-            nd = a.act[x][ai];
-            int first = nd.start / kTile, last = (nd.start + nd.count - 1) / kTile;
-            nt = last - first + 1;
+    for (int c = 0; c < A; c += blockDim.x * kPlanPer) {
+        const int a0 = c + threadIdx.x * kPlanPer;
+        int nt[kPlanPer], sum = 0;
+#pragma unroll
+        for (int r = 0; r < kPlanPer; r++) {
+            nt[r] = 0;
+            if (a0 + r < A) {
+                const Active nd = a.act[x][a0 + r];
+                nt[r] = (nd.start + nd.count - 1) / kTile - nd.start / kTile + 1;
+            }
+            sum += nt[r];
         }
         int tot;
-        int off = block_excl_scan(nt, sh, &tot) + base;
-        if (ai < A) {
+        int off = block_excl_scan(sum, sh, &tot) + base;
+#pragma unroll
+        for (int r = 0; r < kPlanPer; r++) {
+            const int ai = a0 + r;
+            if (ai >= A) break;
+            const Active nd = a.act[x][ai];
             a.tile_base[x][ai] = off;
-            int first = nd.start / kTile;
-            for (int j = 0; j < nt; j++) {
+            const int first = nd.start / kTile;
+            for (int j = 0; j < nt[r]; j++) {
                 if (off + j >= a.tile_cap) { atomicOr(a.err, kErrTileOverflow); break; }
                 Tile t;
                 t.node = ai;
@@ -152,6 +161,7 @@ __device__ void block_plan_tiles(BuildArgs& a, int x, int A)
                 t.first = (j == 0);
                 a.tiles[x][off + j] = t;
             }
+            off += nt[r];
         }
         __syncthreads();
         if (threadIdx.x == 0) base += tot;
@@ -400,11 +410,16 @@ __device__ int block_reduce_sum(int v, int* sh)
     return r;
 }
 
-__global__ void k_select(BuildArgs a, int L)
+constexpr int kSelectThreads = 256;   // k_select's block: 4 histogram bins per thread
+static_assert(4 * kSelectThreads == kSamples, "k_select covers the sample bins with 4 per thread");
+
+__global__ void __launch_bounds__(kSelectThreads) k_select(BuildArgs a, int L)
 {
     __shared__ int s_sel, s_left;
     __shared__ float shf[32];
-    __shared__ int shi[32];
+    __shared__ int shi[33];
+    __shared__ unsigned long long s_key[kSelectThreads / 32];
+    __shared__ int s_c[kSelectThreads / 32];
     const int cur = L & 1;
     const int ai = blockIdx.x;
     if (ai >= a.cnt[kCntActive0 + cur]) return;
@@ -414,41 +429,57 @@ __global__ void k_select(BuildArgs a, int L)
     int mode = a.nmode[ai];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (mode == kModeValue) {
-        if (warp == 0) {
-            const int* nh = a.nhist + (long long)ai * (kSamples + 1);
-            int tot = 0;
-            for (int r = 0; r < 32; r++) {
-                int j = 32 * lane + r;
-                if (j < sp) tot += nh[j];
-            }
-            int c = warp_incl_scan(tot) - tot;
-            unsigned long long best = ~0ull;
-            int best_c = 0;
-            for (int r = 0; r < 32; r++) {
-                int j = 32 * lane + r;
-                if (j < sp) {
-                    c += nh[j];
-                    long long e = 2LL * c - cnt;
-                    if (e < 0) e = -e;
-                    unsigned long long key = ((unsigned long long)e << 11) | (unsigned)j;
-                    if (key < best) {
-                        best = key;
-                        best_c = c;
-                    }
-                }
-            }
-            unsigned long long wbest = best;
+        // thread t holds bins 4t .. 4t+3; c_j = #{x < v_j} is the inclusive
+        // prefix of the histogram up to bin j (a block scan of the thread sums)
+        const int* nh = a.nhist + (long long)ai * (kSamples + 1);
+        int h[4], tot = 0;
 #pragma unroll
-            for (int o = 16; o >= 1; o >>= 1) {
-                unsigned long long ob = __shfl_xor_sync(kFull, wbest, o);
-                wbest = ob < wbest ? ob : wbest;
+        for (int e = 0; e < 4; e++) {
+            const int j = 4 * threadIdx.x + e;
+            h[e] = j < sp ? nh[j] : 0;
+            tot += h[e];
+        }
+        int total;
+        int c = block_excl_scan(tot, shi, &total);
+        // j* = argmin |2 c_j - n|, ties to the smallest j: the minimum key (|.| << 11 | j)
+        unsigned long long best = ~0ull;
+        int best_c = 0;
+#pragma unroll
+        for (int e = 0; e < 4; e++) {
+            const int j = 4 * threadIdx.x + e;
+            c += h[e];
+            long long err = 2LL * c - cnt;
+            if (err < 0) err = -err;
+            const unsigned long long key = ((unsigned long long)err << 11) | (unsigned)j;
+            if (j < sp && key < best) {
+                best = key;
+                best_c = c;
             }
-            int jstar = (int)(wbest & 2047ull);
-            int cstar = __shfl_sync(kFull, best_c, jstar >> 5);
-            if (lane == 0) {
-                s_sel = jstar;
-                s_left = cstar;
+        }
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) {
+            const unsigned long long ob = __shfl_xor_sync(kFull, best, o);
+            const int oc = __shfl_xor_sync(kFull, best_c, o);
+            if (ob < best) {
+                best = ob;
+                best_c = oc;
             }
+        }
+        if (lane == 0) {
+            s_key[warp] = best;
+            s_c[warp] = best_c;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned long long b = s_key[0];
+            int bc = s_c[0];
+            for (int w = 1; w < (int)(blockDim.x >> 5); w++)
+                if (s_key[w] < b) {
+                    b = s_key[w];
+                    bc = s_c[w];
+                }
+            s_sel = (int)(b & 2047ull);
+            s_left = bc;
         }
         __syncthreads();
         if (s_left > 0) {
@@ -516,36 +547,40 @@ __global__ void k_select(BuildArgs a, int L)
 }
 
 // Per-tile count of left points for nodes that span several tiles.
+// Left count of every tile: one block per tile (grid-stride over the tiles),
+// so a level of large nodes keeps many column loads in flight per SM.
 __global__ void k_tilecount(BuildArgs a, int L)
 {
+    __shared__ int sh[33];
     const int cur = L & 1;
-    const int lane = threadIdx.x & 31;
-    const int t = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (t >= a.cnt[kCntTiles0 + cur]) return;
-    const Tile tl = a.tiles[cur][t];
-    const int ai = tl.node;
-    const Active nd = a.act[cur][ai];
-    const int ntiles = a.tile_base[cur][ai + 1] - a.tile_base[cur][ai];
-    int v;
-    if (ntiles == 1) {
-        v = a.nleft[ai];
-    } else if (a.nmode[ai] == kModeIndex) {
-        int half = (nd.count + 1) >> 1;
-        v = min(max(half - (tl.begin - nd.start), 0), tl.end - tl.begin);
-    } else {
+    const int ntl = a.cnt[kCntTiles0 + cur];
+    for (int t = blockIdx.x; t < ntl; t += gridDim.x) {
+        const Tile tl = a.tiles[cur][t];
+        const int ai = tl.node;
+        const Active nd = a.act[cur][ai];
+        const int ntiles = a.tile_base[cur][ai + 1] - a.tile_base[cur][ai];
+        if (ntiles == 1) {
+            if (threadIdx.x == 0) a.tleft[t] = a.nleft[ai];
+            continue;
+        }
+        if (a.nmode[ai] == kModeIndex) {
+            const int half = (nd.count + 1) >> 1;
+            if (threadIdx.x == 0) a.tleft[t] = min(max(half - (tl.begin - nd.start), 0), tl.end - tl.begin);
+            continue;
+        }
         const float s = a.nsplit[ai];
         const float* col = a.X[cur] + (long long)a.ndim[ai] * a.n_pad;
         int c = 0;
-        for (int i4 = (tl.begin & ~3) + 4 * lane; i4 < tl.end; i4 += 128) {
+        for (int i4 = (tl.begin & ~3) + 4 * threadIdx.x; i4 < tl.end; i4 += 4 * blockDim.x) {
             float4 x4 = *reinterpret_cast<const float4*>(col + i4);
             c += (i4 >= tl.begin && i4 < tl.end && x4.x < s);
             c += (i4 + 1 >= tl.begin && i4 + 1 < tl.end && x4.y < s);
             c += (i4 + 2 >= tl.begin && i4 + 2 < tl.end && x4.z < s);
             c += (i4 + 3 >= tl.begin && i4 + 3 < tl.end && x4.w < s);
         }
-        v = warp_sum(c);
+        const int v = block_reduce_sum(c, sh);
+        if (threadIdx.x == 0) a.tleft[t] = v;
     }
-    if (lane == 0) a.tleft[t] = v;
 }
 
 // One block: per-tile left offsets, children creation (next level or subtree
@@ -584,51 +619,55 @@ __global__ void k_children(BuildArgs a, int L)
         s_small = a.cnt[kCntSmall];
     }
     __syncthreads();
-    for (int c0 = 0; c0 < A; c0 += blockDim.x) {
-        const int ai = c0 + threadIdx.x;
-        const bool valid = ai < A;
-        Active nd;
-        int cl = 0, cr = 0, la = 0, ra = 0;
-        if (valid) {
-            nd = a.act[cur][ai];
-            cl = a.nleft[ai];
-            cr = nd.count - cl;
-            la = cl > a.T;
-            ra = cr > a.T;
+    for (int c0 = 0; c0 < A; c0 += blockDim.x * kPlanPer) {
+        // thread t plans nodes a0 .. a0 + kPlanPer - 1: one block scan of its
+        // (children to the next level << 16 | children to the subtree stage);
+        // a pass holds at most 2 kPlanPer blockDim children of either kind < 2^16
+        const int a0 = c0 + threadIdx.x * kPlanPer;
+        int nxt_cnt = 0, sm_cnt = 0;
+#pragma unroll
+        for (int r = 0; r < kPlanPer; r++) {
+            if (a0 + r < A) {
+                const int cl = a.nleft[a0 + r], cr = a.act[cur][a0 + r].count - cl;
+                const int act = (cl > a.T) + (cr > a.T);
+                nxt_cnt += act;
+                sm_cnt += 2 - act;
+            }
         }
-        int ta, ts;
-        int pa = block_excl_scan(la + ra, sh, &ta);
-        int ps = block_excl_scan(valid ? 2 - la - ra : 0, sh, &ts);
-        if (valid) {
+        int tot;
+        const int pk = block_excl_scan((nxt_cnt << 16) | sm_cnt, sh, &tot);
+        int ia = s_next + (pk >> 16), is = s_small + (pk & 0xffff);
+        for (int r = 0; r < kPlanPer; r++) {
+            const int ai = a0 + r;
+            if (ai >= A) break;
+            const Active nd = a.act[cur][ai];
+            const int cl = a.nleft[ai], cr = nd.count - cl;
             const int child = base_id + 2 * ai;
             const int cdepth = nd.depth + 1;
-            const int nbase = s_next + pa, sbase = s_small + ps;
-            int ia = 0, is = 0;
             for (int side = 0; side < 2; side++) {
                 const int cs = side ? nd.start + cl : nd.start;
                 const int cc = side ? cr : cl;
-                const bool act = side ? ra : la;
-                if (act) {
+                if (cc > a.T) {
                     if (cdepth >= kMaxDepth) atomicOr(a.err, kErrDepth);
-                    if (nbase + ia < a.act_cap) {
+                    if (ia < a.act_cap) {
                         Active c;
                         c.start = cs;
                         c.count = cc;
                         c.node = child + side;
                         c.depth = cdepth;
-                        a.act[nxt][nbase + ia] = c;
+                        a.act[nxt][ia] = c;
                     } else {
                         atomicOr(a.err, kErrActiveOverflow);
                     }
                     ia++;
                 } else {
-                    if (sbase + is < a.small_cap) {
-                        Small s;
-                        s.start = cs;
-                        s.count = cc;
-                        s.node = child + side;
-                        s.depth_parity = (cdepth << 1) | nxt;
-                        a.small[sbase + is] = s;
+                    if (is < a.small_cap) {
+                        Small sm;
+                        sm.start = cs;
+                        sm.count = cc;
+                        sm.node = child + side;
+                        sm.depth_parity = (cdepth << 1) | nxt;
+                        a.small[is] = sm;
                     } else {
                         atomicOr(a.err, kErrSmallOverflow);
                     }
@@ -645,8 +684,8 @@ __global__ void k_children(BuildArgs a, int L)
         }
         __syncthreads();
         if (threadIdx.x == 0) {
-            s_next += ta;
-            s_small += ts;
+            s_next += tot >> 16;
+            s_small += tot & 0xffff;
         }
         __syncthreads();
     }
@@ -1298,9 +1337,9 @@ panda_status enqueue_level(BuildState& S, int L, cudaStream_t stream, PhaseTimer
     k_hist<<<tcap, 256, 0, stream>>>(a, L);
     PANDA_LAUNCHED("k_hist");
     timer.begin("level.select");
-    k_select<<<acap, 256, 0, stream>>>(a, L);
+    k_select<<<acap, kSelectThreads, 0, stream>>>(a, L);
     PANDA_LAUNCHED("k_select");
-    k_tilecount<<<(tcap + 7) / 8, 256, 0, stream>>>(a, L);
+    k_tilecount<<<std::min(tcap, 8 * num_sms()), 256, 0, stream>>>(a, L);
     PANDA_LAUNCHED("k_tilecount");
     k_tileoff<<<(acap + 7) / 8, 256, 0, stream>>>(a, L);
     PANDA_LAUNCHED("k_tileoff");
