@@ -909,10 +909,14 @@ __global__ void k_subtree(BuildArgs a, int wbytes)
             const unsigned short* ixc = w.ix[rel & 1];
             unsigned short* ixn = w.ix[(rel + 1) & 1];
             const bool leaf = lc <= a.bucket || depth >= kMaxDepth;
-            // box (and, for inner nodes, the sample variance: every point is a sample)
+            // box (and, for inner nodes, the sample variance: every point is a sample).
+            // The point loops below are unrolled so that each lane has several
+            // independent index and coordinate loads in flight (a lane's sums keep
+            // their order): the stage is latency bound at 12 warps per SM.
             for (int k = 0; k < d; k++) {
                 const float* col = sxo + (size_t)k * TS;
                 float part = 0.0f, mn = INFINITY, mx = -INFINITY;
+#pragma unroll 4
                 for (int j = lane; j < lc; j += 32) {
                     float x = col[ixc[ls + j]];
                     part = __fadd_rn(part, x);
@@ -925,6 +929,7 @@ __global__ void k_subtree(BuildArgs a, int wbytes)
                 if (!leaf) {
                     float mean = __fdiv_rn(fixed_order_warp_total(part), (float)lc);
                     float p2 = 0.0f;
+#pragma unroll 4
                     for (int j = lane; j < lc; j += 32) {
                         float c = __fsub_rn(col[ixc[ls + j]], mean);
                         p2 = __fadd_rn(p2, __fmul_rn(c, c));
@@ -986,6 +991,7 @@ __global__ void k_subtree(BuildArgs a, int wbytes)
                     const uint32_t dmask = (1u << width) - 1u;
                     for (int b = lane; b < 256; b += 32) w.rh[b] = 0;
                     __syncwarp();
+#pragma unroll 4
                     for (int j = lane; j < lc; j += 32) {
                         uint32_t key = float_key(__fadd_rn(col[ixc[ls + j]], 0.0f));
                         if ((key & mask) == prefix) atomicAdd(&w.rh[(key >> shift) & dmask], 1);
@@ -1021,6 +1027,7 @@ __global__ void k_subtree(BuildArgs a, int wbytes)
                 const float vp = key_float(prefix);
                 int na = 0, nb = 0;
                 float up = INFINITY;
+#pragma unroll 4
                 for (int j = lane; j < lc; j += 32) {
                     float x = col[ixc[ls + j]];
                     na += x < vp;
