@@ -1138,11 +1138,13 @@ __global__ void k_subtree(BuildArgs a, int wbytes)
 }
 
 // Bottom-up boxes of the level-stage nodes: union of the two children.
-__global__ void k_boxes(BuildArgs a, int nlevels)
+// Levels L_hi down to L_lo; a launch covers several levels only as one block
+// (the block barrier orders them), a grid covers one level.
+__global__ void k_boxes(BuildArgs a, int L_hi, int L_lo)
 {
-    for (int L = nlevels - 1; L >= 0; L--) {
+    for (int L = L_hi; L >= L_lo; L--) {
         const int A = a.lvl_count[L];
-        for (int i = threadIdx.x; i < A; i += blockDim.x) {
+        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < A; i += gridDim.x * blockDim.x) {
             const int node = a.lvl_nodes[L * a.lvl_stride + i];
             if (node >= a.node_cap) continue;
             float* rec = reinterpret_cast<float*>(a.nodes + (long long)node * a.ns);
@@ -1369,8 +1371,18 @@ panda_status enqueue_finish(BuildState& S, int nlevels, cudaStream_t stream, Pha
     k_subtree<<<sms, wpb * 32, (size_t)wpb * wb, stream>>>(a, wb);
     PANDA_LAUNCHED("k_subtree");
     timer.begin("boxes");
-    if (nlevels > 0) {
-        k_boxes<<<1, 1024, 0, stream>>>(a, nlevels);
+    // bottom-up: a level with more nodes than one block covers at once gets a
+    // grid of its own, the levels above it go together in one block
+    int L = nlevels - 1;
+    for (; L >= 0; L--) {
+        const long long bound = std::min<long long>(
+            L < 30 ? (1LL << L) * std::max(1, a.set_off ? a.nsets : 1) : (1LL << 30), S.pl.act_cap);
+        if (bound <= 1024) break;
+        k_boxes<<<(unsigned)((bound + 255) / 256), 256, 0, stream>>>(a, L, L);
+        PANDA_LAUNCHED("k_boxes");
+    }
+    if (L >= 0) {
+        k_boxes<<<1, 1024, 0, stream>>>(a, L, 0);
         PANDA_LAUNCHED("k_boxes");
     }
     timer.end();
