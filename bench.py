@@ -373,7 +373,7 @@ def run_ours(args):
     end.record(stream)
     torch.cuda.synchronize()
     barrier()
-    launches = P.kernel_launches() - l0
+    timed_launches = P.kernel_launches() - l0
     clk = clocks.stop()
     P.set_phase_timing(False)
     el_ms = start.elapsed_time(end)
@@ -477,10 +477,10 @@ def run_ours(args):
         if ph not in per_step or per_step[ph][0] <= 0:
             continue
         byts, desc = build_algorithmic_bytes(ph, act, n, d, info)
-        ms, launches = per_step[ph]
-        ach = byts / (ms / 1e3) / 1e9
+        ph_ms, ph_launches = per_step[ph]
+        ach = byts / (ph_ms / 1e3) / 1e9
         build_roof[kernel_phases[ph]] = {"achieved": ach, "frac": ach / hbm_peak, "unit": "GB/s",
-                                         "ms_per_step": ms, "launches_per_step": launches,
+                                         "ms_per_step": ph_ms, "launches_per_step": ph_launches,
                                          "bytes_per_step": byts, "algorithmic": desc}
     if dom != "query.traverse":
         b = build_roof[kernel_phases[dom]]
@@ -501,7 +501,7 @@ def run_ours(args):
             "config": dict(workload_config(w, args.order),
                            query_path="panda_knn_self (all-points query: the tree's packed points in leaf "
                                       "order are the queries)" if use_self else "panda_knn (query buffer)"),
-            "clocks": clk, "e2e": e2e, "gpu_launches": launches, "general_query_path": general,
+            "clocks": clk, "e2e": e2e, "gpu_launches": timed_launches, "general_query_path": general,
             "roofline": roof, "cpu_baseline": cpu,
             "build_pts_per_s": world * n / (build_ms / 1e3), "query_per_s": world * m / (query_ms / 1e3),
             "build_ms": build_ms, "query_ms": query_ms,
