@@ -356,6 +356,18 @@ panda_status panda_knn_visits(const panda_tree* tree, const float* queries, int6
                               uint64_t* out_stats, const panda_query_params* params, void* stream);
 /* Number of kernels this library launched on this thread so far. */
 int64_t panda_kernel_launches(void);
+/* Fault injection for tests of the host-side error paths (no GPU fault is
+ * involved): after `after` >= 0 further device workspace allocations (the
+ * stream-ordered pool: scratch, staging buffers, tree tables) succeed, the
+ * next one fails as if the device were out of memory -- the call returns
+ * PANDA_ERR_OUT_OF_MEMORY, frees what it held and launches nothing on the
+ * missing buffer -- and injection is off again; `after` < 0 turns it off.
+ * Process-wide.  panda_debug_pool_used synchronises the current device and
+ * writes the bytes currently allocated from its stream-ordered pool (what
+ * the library holds: trees and workspace), so a test can check that a failed
+ * call leaked nothing. */
+panda_status panda_debug_fail_alloc(int64_t after);
+panda_status panda_debug_pool_used(int64_t* bytes);
 
 const char* panda_status_string(panda_status status);
 const char* panda_last_error(void); /* thread-local; "" if none */

@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -28,6 +29,9 @@ struct PhaseRow {
 thread_local std::vector<PhaseRow> g_phases;
 
 std::once_flag g_pool_once[64];
+// Fault injection for the host-side error paths: workspace allocations left
+// before the next one fails (-1: none fails).
+std::atomic<long long> g_fail_after{-1};
 int g_sms[64] = {0};
 }  // namespace
 
@@ -144,6 +148,13 @@ panda_status ws_alloc(void** p, size_t bytes, cudaStream_t s, const char* what)
         });
     }
     *p = nullptr;
+    long long f = g_fail_after.load();
+    while (f >= 0 && !g_fail_after.compare_exchange_weak(f, f - 1)) {
+    }
+    if (f == 0) {
+        set_error("allocating %zu bytes for %s: injected allocation failure", bytes, what);
+        return PANDA_ERR_OUT_OF_MEMORY;
+    }
     cudaError_t e = cudaMallocAsync(p, bytes, s);
     if (e != cudaSuccess) {
         *p = nullptr;
@@ -225,6 +236,31 @@ panda_status panda_build_async(const float* points, int64_t n, int32_t d, int32_
         set_error("panda_build: host exception");
         return PANDA_ERR_OUT_OF_MEMORY;
     }
+}
+
+panda_status panda_debug_fail_alloc(int64_t after)
+{
+    g_fail_after.store(after < 0 ? -1 : (long long)after);
+    return PANDA_OK;
+}
+
+panda_status panda_debug_pool_used(int64_t* bytes)
+{
+    clear_error();
+    if (!bytes) {
+        set_error("panda_debug_pool_used: invalid argument");
+        return PANDA_ERR_INVALID_ARGUMENT;
+    }
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    cudaMemPool_t pool;
+    if (e == cudaSuccess) e = cudaDeviceGetDefaultMemPool(&pool, dev);
+    uint64_t used = 0;
+    if (e == cudaSuccess) e = cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &used);
+    if (e != cudaSuccess) return cuda_fail(e, "panda_debug_pool_used");
+    *bytes = (int64_t)used;
+    return PANDA_OK;
 }
 
 panda_status panda_build(const float* points, int64_t n, int32_t d, int32_t bucket, panda_tree** out)
@@ -470,8 +506,16 @@ void panda_free(panda_tree* tree)
     cudaGetDevice(&cur);
     if (cur != tree->device) cudaSetDevice(tree->device);
     cudaDeviceSynchronize();
-    if (tree->nodes) cudaFree(tree->nodes);
-    if (tree->points) cudaFree(tree->points);
+    if (tree->pooled) {
+        // stream-ordered pool memory goes back to its pool with cudaFreeAsync
+        // (after cudaFree the pool still counted a freed tree as in use)
+        if (tree->nodes) cudaFreeAsync(tree->nodes, 0);
+        if (tree->points) cudaFreeAsync(tree->points, 0);
+        cudaStreamSynchronize(0);
+    } else {
+        if (tree->nodes) cudaFree(tree->nodes);
+        if (tree->points) cudaFree(tree->points);
+    }
     cudaGetLastError();
     if (cur != tree->device) cudaSetDevice(cur);
     delete tree;

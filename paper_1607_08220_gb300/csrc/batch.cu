@@ -424,8 +424,10 @@ void panda_batch_free(panda_batch* b)
     if (b->exec) cudaGraphExecDestroy(b->exec);
     forest_destroy(b->bs, nullptr);
     cudaDeviceSynchronize();
-    if (b->forest.nodes) cudaFree(b->forest.nodes);
-    if (b->forest.points) cudaFree(b->forest.points);
+    // the forest's tables come from the stream-ordered pool
+    if (b->forest.nodes) cudaFreeAsync(b->forest.nodes, 0);
+    if (b->forest.points) cudaFreeAsync(b->forest.points, 0);
+    cudaStreamSynchronize(0);
     b->forest.nodes = nullptr;
     b->forest.points = nullptr;
     for (void* p : b->owned) cudaFree(p);

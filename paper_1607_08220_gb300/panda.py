@@ -69,6 +69,8 @@ SIGNATURES = {
     "panda_set_phase_timing": ([_I32], None),
     "panda_phase_times": ([_P, _P, _P, _I32], _I32),
     "panda_kernel_launches": ([], _I64),
+    "panda_debug_fail_alloc": ([_I64], ctypes.c_int),
+    "panda_debug_pool_used": ([_P], ctypes.c_int),
     "panda_status_string": ([ctypes.c_int], ctypes.c_char_p),
     "panda_last_error": ([], ctypes.c_char_p),
     "panda_version": ([], ctypes.c_char_p),
@@ -655,6 +657,21 @@ def phase_times() -> list[tuple[str, float, int]]:
 
 def kernel_launches() -> int:
     return int(load().panda_kernel_launches())
+
+
+def debug_fail_alloc(after: int) -> None:
+    """Fault injection for tests: after `after` more device workspace
+    allocations succeed, the next fails as out of memory (then injection is
+    off again); a negative value turns it off."""
+    _check(load().panda_debug_fail_alloc(int(after)))
+
+
+def debug_pool_used() -> int:
+    """Bytes the library holds in the device's stream-ordered pool (the
+    device is synchronised first)."""
+    v = ctypes.c_int64(0)
+    _check(load().panda_debug_pool_used(ctypes.byref(v)))
+    return int(v.value)
 
 
 def version() -> str:
