@@ -583,8 +583,6 @@ __global__ void k_tilecount(BuildArgs a, int L)
     }
 }
 
-// One block: per-tile left offsets, children creation (next level or subtree
-// stage), node headers of this level, tile plan of the next level.
 // Left-count offsets of every node's tiles (exclusive scan of the per-tile
 // left counts within the node), one warp per node over the whole grid.
 __global__ void k_tileoff(BuildArgs a, int L)
@@ -607,6 +605,8 @@ __global__ void k_tileoff(BuildArgs a, int L)
     if (lane == 0 && running != a.nleft[ai]) atomicOr(a.err, kErrInternal);
 }
 
+// One block: children creation (next level or subtree stage), node headers of
+// this level, tile plan of the next level.
 __global__ void k_children(BuildArgs a, int L)
 {
     __shared__ int sh[33];
