@@ -26,13 +26,22 @@
  *     (pinned or pageable) and copy in and out themselves.
  *   - `stream` arguments are cudaStream_t values passed as void*; NULL is
  *     the legacy default stream.
- *   - Outputs are caller-allocated.  No exception crosses this ABI.  On any
- *     error the outputs are unspecified and the tree handle is not created.
+ *   - Outputs are caller-allocated.  No exception crosses this ABI.  No
+ *     partial output survives an error: argument errors are found before
+ *     anything is enqueued and leave every output untouched; a blocking
+ *     device-pointer query (panda_knn, panda_knn_self) that finds a
+ *     non-finite query or fails a consistency check after its kernels ran
+ *     overwrites every output row with (id -1, d2 +inf); the _host variants
+ *     then leave the host outputs untouched; a failed build creates no
+ *     handle.  The _async variants return once their work is enqueued and
+ *     report no data error.
  *   - Every CUDA failure is reported as PANDA_ERR_CUDA; panda_last_error()
  *     returns the message of the last failure on the calling thread.
  *   - A tree is immutable after its build: concurrent panda_knn calls on one
- *     tree from several streams are allowed.  panda_free must not run while
- *     work that reads the tree is in flight.
+ *     tree from several streams are allowed.  Every call that enqueues work
+ *     on a tree records it (one CUDA event per call); panda_free and
+ *     panda_free_async make the GPU wait for that work before the memory goes
+ *     back to the pool, so the host never waits in a free.
  *   - Valid ranges: 1 <= n < 2^31, 1 <= d <= 16, 1 <= bucket <= 256,
  *     1 <= k <= 64, m >= 0 (m = 0 does nothing).  Out-of-range values give
  *     PANDA_ERR_INVALID_ARGUMENT (or PANDA_ERR_UNSUPPORTED for d > 16,
@@ -193,25 +202,36 @@ panda_status panda_knn_vote(const int32_t* ids, int64_t m, int32_t k, const int3
 panda_status panda_knn_mean(const int32_t* ids, int64_t m, int32_t k, const float* values, int64_t n,
                             float* out_values, void* stream);
 
-/* Same query as panda_knn_async (default parameters) for callers that cannot
- * allocate device memory while they query.  No counterpart in the paper: the
- * query ordering's scratch space is a fixed file-scope device array (12.6 MB,
- * present on every device that loads the library until exit) instead of
- * stream-ordered allocations, so the call makes no cudaMalloc/cudaFree and
- * calls no allocating library routine.  m is limited to 1048576 (2^20)
- * queries per call; larger m returns PANDA_ERR_UNSUPPORTED.  All calls share
- * the array: calls that overlap on the GPU race, so serialise them (one
- * stream).  The first call on a device looks up the array's address; make it
- * before any stream capture.  Non-finite queries are not reported. */
+/* The same answers as panda_knn_async (default parameters) for callers that
+ * cannot allocate device memory while they query.  No counterpart in the
+ * paper: the query ordering's scratch space is a fixed file-scope device array
+ * (12.6 MB, present on every device that loads the library until exit)
+ * instead of stream-ordered allocations, so the call makes no
+ * cudaMalloc/cudaFree and calls no allocating library routine.  m is limited
+ * to 1048576 (2^20) queries per call; larger m returns PANDA_ERR_UNSUPPORTED.
+ * All calls share the array: calls that overlap on the GPU race, so serialise
+ * them (one stream).  The first call on a device looks up the array's address;
+ * make it before any stream capture.  The address is cached per device for the
+ * life of the process and does not survive cudaDeviceReset.  Differences from
+ * panda_knn_async, none of which changes a result: the leaf-ordering histogram
+ * has at most 2^20 - 1 bins (2^22 there), dense query sets (2m >= n) keep
+ * 32-query packets instead of one bin's queries per warp (panda_knn_async's
+ * job list), non-finite queries are not reported, and the call records no use
+ * of the tree (that takes an event): free the tree only once `stream` has
+ * passed this call. */
 panda_status panda_knn_noalloc(const panda_tree* tree, const float* queries, int64_t m, int32_t k,
                                int32_t* out_ids, float* out_d2, void* stream);
 
-/* Releases the tree's device memory (NULL-safe). */
+/* Releases the tree (NULL-safe).  The handle is gone at once; the device
+ * memory returns to the stream-ordered pool, in the order of the legacy
+ * default stream, after every recorded use of the tree (its build, each query
+ * and refit, on whatever stream they ran) has finished on the GPU.  The host
+ * does not wait.  Trees read by panda_tree_load (cudaMalloc'd tables) are
+ * released with cudaFree, which waits for the device. */
 void panda_free(panda_tree* tree);
-/* Stream-ordered free: the tree's device memory returns to the pool once the
- * work queued on `stream` before the call (queries of this tree on other
- * streams must be ordered before it by the caller) has run; the handle is
- * gone at once.  Trees read by panda_tree_load are freed as by panda_free. */
+/* The same, in the order of `stream`: the memory returns to the pool after
+ * the work queued on `stream` before the call and every recorded use of the
+ * tree have run. */
 void panda_free_async(panda_tree* tree, void* stream);
 
 /* ---- batched form: many independent point sets, Sec. III-B (query batching) ---
@@ -362,10 +382,11 @@ int64_t panda_kernel_launches(void);
  * next one fails as if the device were out of memory -- the call returns
  * PANDA_ERR_OUT_OF_MEMORY, frees what it held and launches nothing on the
  * missing buffer -- and injection is off again; `after` < 0 turns it off.
- * Process-wide.  panda_debug_pool_used synchronises the current device and
- * writes the bytes currently allocated from its stream-ordered pool (what
- * the library holds: trees and workspace), so a test can check that a failed
- * call leaked nothing. */
+ * Process-wide.  panda_debug_pool_used writes the bytes the library holds in
+ * the stream-ordered pool right now (its own count of live allocations:
+ * trees, the batched form's forest and every call's workspace, on all
+ * devices; memory the pool caches for reuse and other users' allocations
+ * are not counted), so a test can check that a failed call leaked nothing. */
 panda_status panda_debug_fail_alloc(int64_t after);
 panda_status panda_debug_pool_used(int64_t* bytes);
 

@@ -67,33 +67,60 @@ def _load():
     with _lock:
         if _lib is not None:
             return _lib
-        L = ctypes.CDLL(compile_oracle())
-        P = ctypes.c_void_p
-        i32, i64 = ctypes.c_int32, ctypes.c_int64
-        L.or_build.argtypes = [P, i64, i32, i32, ctypes.POINTER(P)]
-        L.or_build.restype = ctypes.c_int
-        L.or_free.argtypes = [P]
-        L.or_free.restype = None
-        L.or_tree_num_nodes.argtypes = [P]
-        L.or_tree_num_nodes.restype = i64
-        L.or_tree_depth.argtypes = [P]
-        L.or_tree_depth.restype = i32
-        L.or_tree_export.argtypes = [P, P, P, P, P, P, P]
-        L.or_tree_export.restype = None
-        L.or_knn.argtypes = [P, P, i64, i32, P, P, P, i32]
-        L.or_knn.restype = ctypes.c_int
-        L.or_knn_r.argtypes = [P, P, i64, i32, ctypes.c_float, P, P, P, i32]
-        L.or_knn_r.restype = ctypes.c_int
-        L.or_brute_knn.argtypes = [P, i64, i32, P, i64, i32, P, P, i32]
-        L.or_brute_knn.restype = ctypes.c_int
-        L.or_brute_knn_r.argtypes = [P, i64, i32, P, i64, i32, ctypes.c_float, P, P, i32]
-        L.or_brute_knn_r.restype = ctypes.c_int
-        L.or_brute_knn_rows.argtypes = [P, i64, i32, P, P, i64, i32, P, P, i32]
-        L.or_brute_knn_rows.restype = ctypes.c_int
-        L.or_max_depth.restype = i32
-        L.or_sample_count.restype = i32
-        _lib = L
-        return L
+        _lib = _bind(ctypes.CDLL(compile_oracle()))
+        return _lib
+
+
+def compile_variant(source: str, tag: str):
+    """Compile `source` (a modified copy of panda_oracle.c) with the oracle's
+    flags and return the loaded library.  For tests that plant a mistake in
+    the oracle and check that a pin catches it; the oracle itself is never
+    modified."""
+    os.makedirs(_BUILD_DIR, exist_ok=True)
+    h = hashlib.sha1(source.encode() + " ".join(CFLAGS).encode()).hexdigest()[:12]
+    path = os.path.join(_BUILD_DIR, f"libpanda_oracle_variant_{tag}_{h}.so")
+    if not os.path.exists(path):
+        src = path[:-3] + ".c"
+        with open(src, "w") as f:
+            f.write(source)
+        tmp = path + f".tmp{os.getpid()}"
+        subprocess.run(["gcc", *CFLAGS, "-o", tmp, src, "-lm"], check=True)
+        os.replace(tmp, path)
+    return _bind(ctypes.CDLL(path))
+
+
+def source_text() -> str:
+    with open(_SRC) as f:
+        return f.read()
+
+
+def _bind(L):
+    """Declare the C signatures on a loaded oracle library."""
+    P = ctypes.c_void_p
+    i32, i64 = ctypes.c_int32, ctypes.c_int64
+    L.or_build.argtypes = [P, i64, i32, i32, ctypes.POINTER(P)]
+    L.or_build.restype = ctypes.c_int
+    L.or_free.argtypes = [P]
+    L.or_free.restype = None
+    L.or_tree_num_nodes.argtypes = [P]
+    L.or_tree_num_nodes.restype = i64
+    L.or_tree_depth.argtypes = [P]
+    L.or_tree_depth.restype = i32
+    L.or_tree_export.argtypes = [P, P, P, P, P, P, P]
+    L.or_tree_export.restype = None
+    L.or_knn.argtypes = [P, P, i64, i32, P, P, P, i32]
+    L.or_knn.restype = ctypes.c_int
+    L.or_knn_r.argtypes = [P, P, i64, i32, ctypes.c_float, P, P, P, i32]
+    L.or_knn_r.restype = ctypes.c_int
+    L.or_brute_knn.argtypes = [P, i64, i32, P, i64, i32, P, P, i32]
+    L.or_brute_knn.restype = ctypes.c_int
+    L.or_brute_knn_r.argtypes = [P, i64, i32, P, i64, i32, ctypes.c_float, P, P, i32]
+    L.or_brute_knn_r.restype = ctypes.c_int
+    L.or_brute_knn_rows.argtypes = [P, i64, i32, P, P, i64, i32, P, P, i32]
+    L.or_brute_knn_rows.restype = ctypes.c_int
+    L.or_max_depth.restype = i32
+    L.or_sample_count.restype = i32
+    return L
 
 
 def _ptr(a: np.ndarray):
@@ -116,23 +143,25 @@ def sample_count() -> int:
 class Tree:
     """Oracle kd-tree (owns a C handle)."""
 
-    def __init__(self, handle, n: int, d: int, bucket: int):
+    def __init__(self, handle, n: int, d: int, bucket: int, lib=None):
         self._h = handle
+        self._L = lib if lib is not None else _lib
         self.n, self.d, self.bucket = n, d, bucket
 
     def __del__(self):
         h = getattr(self, "_h", None)
-        if h and _lib is not None:
-            _lib.or_free(h)
+        L = getattr(self, "_L", None)
+        if h and L is not None:
+            L.or_free(h)
             self._h = None
 
     @property
     def num_nodes(self) -> int:
-        return int(_lib.or_tree_num_nodes(self._h))
+        return int(self._L.or_tree_num_nodes(self._h))
 
     @property
     def depth(self) -> int:
-        return int(_lib.or_tree_depth(self._h))
+        return int(self._L.or_tree_depth(self._h))
 
     def export(self) -> dict:
         """Node table in preorder plus the leaf-order permutation."""
@@ -143,23 +172,24 @@ class Tree:
         lo = np.empty((nn, d), np.float32)
         hi = np.empty((nn, d), np.float32)
         perm = np.empty(self.n, np.int32)
-        _lib.or_tree_export(self._h, _ptr(meta), _ptr(split), _ptr(rng), _ptr(lo), _ptr(hi), _ptr(perm))
+        self._L.or_tree_export(self._h, _ptr(meta), _ptr(split), _ptr(rng), _ptr(lo), _ptr(hi), _ptr(perm))
         return dict(leaf=meta[:, 0].astype(bool), index_split=meta[:, 1].astype(bool),
                     dim=meta[:, 2].copy(), depth=meta[:, 3].copy(), split=split,
                     start=rng[:, 0].copy(), count=rng[:, 1].copy(), left=rng[:, 2].copy(),
                     right=rng[:, 3].copy(), lo=lo, hi=hi, perm=perm)
 
 
-def build(points: np.ndarray, bucket: int = 32) -> Tree:
-    """kd-tree over host points [n][d] (float32)."""
-    L = _load()
+def build(points: np.ndarray, bucket: int = 32, lib=None) -> Tree:
+    """kd-tree over host points [n][d] (float32).  `lib`: a library from
+    compile_variant (tests of planted mistakes); the oracle by default."""
+    L = lib if lib is not None else _load()
     pts = np.ascontiguousarray(points, dtype=np.float32)
     if pts.ndim != 2:
         raise ValueError("points must be [n][d]")
     n, d = pts.shape
     h = ctypes.c_void_p()
     _check(L.or_build(_ptr(pts), n, d, int(bucket), ctypes.byref(h)))
-    return Tree(h, n, d, bucket)
+    return Tree(h, n, d, bucket, L)
 
 
 def knn(tree: Tree, queries: np.ndarray, k: int, threads: int = 0, visits: bool = False, max_d2=None):
@@ -173,7 +203,7 @@ def knn(tree: Tree, queries: np.ndarray, k: int, threads: int = 0, visits: bool 
     d2 = np.empty((m, k), np.float32)
     v = np.empty((m, 2), np.int64) if visits else None
     r2 = np.float32(np.inf if max_d2 is None else max_d2)
-    _check(_lib.or_knn_r(tree._h, _ptr(q), m, int(k), ctypes.c_float(r2), _ptr(ids), _ptr(d2),
+    _check(tree._L.or_knn_r(tree._h, _ptr(q), m, int(k), ctypes.c_float(r2), _ptr(ids), _ptr(d2),
                          _ptr(v) if v is not None else None, int(threads)))
     return (ids, d2, v) if visits else (ids, d2)
 

@@ -8,6 +8,7 @@
 #include <atomic>
 #include <mutex>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "common.cuh"
@@ -33,6 +34,12 @@ std::once_flag g_pool_once[64];
 // before the next one fails (-1: none fails).
 std::atomic<long long> g_fail_after{-1};
 int g_sms[64] = {0};
+// Live workspace and tree allocations of the library: pointer -> bytes.
+std::mutex g_ws_mu;
+std::unordered_map<void*, size_t> g_ws_live;
+long long g_ws_bytes = 0;
+// Guards the use-event lists of every tree.
+std::mutex g_use_mu;
 }  // namespace
 
 void set_error(const char* fmt, ...)
@@ -162,12 +169,85 @@ panda_status ws_alloc(void** p, size_t bytes, cudaStream_t s, const char* what)
         cudaGetLastError();
         return e == cudaErrorMemoryAllocation ? PANDA_ERR_OUT_OF_MEMORY : PANDA_ERR_CUDA;
     }
+    try {
+        std::lock_guard<std::mutex> lk(g_ws_mu);
+        g_ws_live[*p] = bytes;
+        g_ws_bytes += (long long)bytes;
+    } catch (...) {
+        cudaFreeAsync(*p, s);
+        *p = nullptr;
+        set_error("allocating %zu bytes for %s: host bookkeeping failed", bytes, what);
+        return PANDA_ERR_OUT_OF_MEMORY;
+    }
     return PANDA_OK;
 }
 
 void ws_free(void* p, cudaStream_t s)
 {
-    if (p) cudaFreeAsync(p, s);
+    if (!p) return;
+    {
+        std::lock_guard<std::mutex> lk(g_ws_mu);
+        auto it = g_ws_live.find(p);
+        if (it != g_ws_live.end()) {
+            g_ws_bytes -= (long long)it->second;
+            g_ws_live.erase(it);
+        }
+    }
+    cudaFreeAsync(p, s);
+}
+
+long long ws_bytes_held()
+{
+    std::lock_guard<std::mutex> lk(g_ws_mu);
+    return g_ws_bytes;
+}
+
+void note_tree_use(const panda_tree* ct, cudaStream_t s)
+{
+    if (!ct) return;
+    panda_tree* t = const_cast<panda_tree*>(ct);
+    std::lock_guard<std::mutex> lk(g_use_mu);
+    // drop the uses that have finished
+    int w = 0;
+    for (int i = 0; i < t->nuses; i++) {
+        if (cudaEventQuery(t->uses[i]) == cudaSuccess) cudaEventDestroy(t->uses[i]);
+        else t->uses[w++] = t->uses[i];
+    }
+    cudaGetLastError();
+    t->nuses = w;
+    if (t->nuses == panda_tree::kMaxUses) {
+        // list full: wait for the oldest on the host (rare: kMaxUses uses still in flight)
+        cudaEventSynchronize(t->uses[0]);
+        cudaEventDestroy(t->uses[0]);
+        for (int i = 1; i < t->nuses; i++) t->uses[i - 1] = t->uses[i];
+        t->nuses--;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventRecord(e, s) != cudaSuccess) {
+        // no event: fall back to waiting for the stream now
+        if (e) cudaEventDestroy(e);
+        cudaGetLastError();
+        cudaStreamSynchronize(s);
+        cudaGetLastError();
+        return;
+    }
+    t->uses[t->nuses++] = e;
+}
+
+void wait_tree_uses(const panda_tree* ct, cudaStream_t s)
+{
+    panda_tree* t = const_cast<panda_tree*>(ct);
+    std::lock_guard<std::mutex> lk(g_use_mu);
+    for (int i = 0; i < t->nuses; i++) {
+        if (cudaStreamWaitEvent(s, t->uses[i], 0) != cudaSuccess) {
+            cudaGetLastError();
+            cudaEventSynchronize(t->uses[i]);
+        }
+        cudaEventDestroy(t->uses[i]);
+    }
+    cudaGetLastError();
+    t->nuses = 0;
 }
 
 bool is_device_ptr(const void* p)
@@ -179,6 +259,26 @@ bool is_device_ptr(const void* p)
         return false;
     }
     return attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
+}
+
+// Overwrite a failed query's device outputs with the padding row (-1, +inf),
+// so a blocking call that reports an error never leaves partial results.
+__global__ void k_fill_failed(int32_t* ids, float* d2, long long count)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+         i += (long long)gridDim.x * blockDim.x) {
+        ids[i] = -1;
+        d2[i] = __int_as_float(0x7f800000);
+    }
+}
+
+void clear_failed_outputs(int32_t* ids, float* d2, long long count)
+{
+    if (!ids || !d2 || count <= 0) return;
+    const unsigned blocks = (unsigned)std::min<long long>((count + 255) / 256, 4LL * num_sms());
+    k_fill_failed<<<blocks, 256>>>(ids, d2, count);
+    cudaStreamSynchronize(nullptr);
+    cudaGetLastError();
 }
 
 }  // namespace panda
@@ -251,15 +351,7 @@ panda_status panda_debug_pool_used(int64_t* bytes)
         set_error("panda_debug_pool_used: invalid argument");
         return PANDA_ERR_INVALID_ARGUMENT;
     }
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceSynchronize();
-    cudaMemPool_t pool;
-    if (e == cudaSuccess) e = cudaDeviceGetDefaultMemPool(&pool, dev);
-    uint64_t used = 0;
-    if (e == cudaSuccess) e = cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &used);
-    if (e != cudaSuccess) return cuda_fail(e, "panda_debug_pool_used");
-    *bytes = (int64_t)used;
+    *bytes = (int64_t)ws_bytes_held();
     return PANDA_OK;
 }
 
@@ -329,6 +421,7 @@ panda_status panda_knn(const panda_tree* tree, const float* queries, int64_t m, 
         set_error("panda_knn: host exception");
         return PANDA_ERR_OUT_OF_MEMORY;
     }
+    if (s == PANDA_OK && herr) clear_failed_outputs(out_ids, out_d2, m * (long long)k);
     if (s == PANDA_OK && (herr & kErrNonfinite)) {
         set_error("panda_knn: non-finite query coordinate");
         return PANDA_ERR_NONFINITE_INPUT;
@@ -364,6 +457,7 @@ panda_status panda_knn_self(const panda_tree* tree, int32_t k, int32_t* out_ids,
         return PANDA_ERR_OUT_OF_MEMORY;
     }
     if (s == PANDA_OK && herr) {
+        clear_failed_outputs(out_ids, out_d2, tree->n * (long long)k);
         set_error("panda_knn_self: internal consistency check failed (0x%x)", herr);
         return PANDA_ERR_CUDA;
     }
@@ -397,7 +491,7 @@ static panda_status knn_self_host_impl(const panda_tree* tree, int32_t k, int32_
             st = PANDA_ERR_OUT_OF_MEMORY;
         }
     }
-    if (st == PANDA_OK) {
+    if (st == PANDA_OK && !herr) {   // a failed query leaves the host outputs untouched
         cudaError_t e = cudaMemcpyAsync(out_ids, di, ob, cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaMemcpyAsync(out_d2, dd, ob, cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess && wait) e = cudaStreamSynchronize(s);
@@ -457,7 +551,7 @@ panda_status panda_knn_host(const panda_tree* tree, const float* queries, int64_
             st = PANDA_ERR_OUT_OF_MEMORY;
         }
     }
-    if (st == PANDA_OK) {
+    if (st == PANDA_OK && !herr) {   // a failed query leaves the host outputs untouched
         e = cudaMemcpyAsync(out_ids, di, ob, cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaMemcpyAsync(out_d2, dd, ob, cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -469,6 +563,10 @@ panda_status panda_knn_host(const panda_tree* tree, const float* queries, int64_
     if (st == PANDA_OK && (herr & kErrNonfinite)) {
         set_error("panda_knn_host: non-finite query coordinate");
         return PANDA_ERR_NONFINITE_INPUT;
+    }
+    if (st == PANDA_OK && herr) {
+        set_error("panda_knn_host: internal consistency check failed (0x%x)", herr);
+        return PANDA_ERR_CUDA;
     }
     return st;
 }
@@ -499,20 +597,21 @@ panda_status panda_knn_visits(const panda_tree* tree, const float* queries, int6
     }
 }
 
-void panda_free(panda_tree* tree)
+// Frees wait, on the GPU, for every recorded use of the tree (the build, each
+// query and refit), then return the memory to the pool in stream order; the
+// host does not wait.
+static void free_tree_on(panda_tree* tree, cudaStream_t s)
 {
-    if (!tree) return;
     int cur = 0;
     cudaGetDevice(&cur);
     if (cur != tree->device) cudaSetDevice(tree->device);
-    cudaDeviceSynchronize();
     if (tree->pooled) {
-        // stream-ordered pool memory goes back to its pool with cudaFreeAsync
-        // (after cudaFree the pool still counted a freed tree as in use)
-        if (tree->nodes) cudaFreeAsync(tree->nodes, 0);
-        if (tree->points) cudaFreeAsync(tree->points, 0);
-        cudaStreamSynchronize(0);
+        wait_tree_uses(tree, s);
+        ws_free(tree->nodes, s);
+        ws_free(tree->points, s);
     } else {
+        // cudaMalloc'd tables (a loaded checkpoint): cudaFree waits for the device
+        wait_tree_uses(tree, s);
         if (tree->nodes) cudaFree(tree->nodes);
         if (tree->points) cudaFree(tree->points);
     }
@@ -521,22 +620,16 @@ void panda_free(panda_tree* tree)
     delete tree;
 }
 
+void panda_free(panda_tree* tree)
+{
+    if (!tree) return;
+    free_tree_on(tree, nullptr);
+}
+
 void panda_free_async(panda_tree* tree, void* stream)
 {
     if (!tree) return;
-    if (!tree->pooled) {   // not from the stream-ordered pool: the blocking free
-        panda_free(tree);
-        return;
-    }
-    int cur = 0;
-    cudaGetDevice(&cur);
-    if (cur != tree->device) cudaSetDevice(tree->device);
-    cudaStream_t s = (cudaStream_t)stream;
-    if (tree->nodes) cudaFreeAsync(tree->nodes, s);
-    if (tree->points) cudaFreeAsync(tree->points, s);
-    cudaGetLastError();
-    if (cur != tree->device) cudaSetDevice(cur);
-    delete tree;
+    free_tree_on(tree, (cudaStream_t)stream);
 }
 
 panda_status panda_tree_get_info(const panda_tree* t, panda_tree_info* info)

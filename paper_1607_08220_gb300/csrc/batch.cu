@@ -425,8 +425,8 @@ void panda_batch_free(panda_batch* b)
     forest_destroy(b->bs, nullptr);
     cudaDeviceSynchronize();
     // the forest's tables come from the stream-ordered pool
-    if (b->forest.nodes) cudaFreeAsync(b->forest.nodes, 0);
-    if (b->forest.points) cudaFreeAsync(b->forest.points, 0);
+    ws_free(b->forest.nodes, nullptr);
+    ws_free(b->forest.points, nullptr);
     cudaStreamSynchronize(0);
     b->forest.nodes = nullptr;
     b->forest.points = nullptr;

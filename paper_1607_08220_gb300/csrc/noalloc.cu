@@ -4,12 +4,17 @@
 // under an allocator it does not own (a host runtime that has reserved the
 // whole device, or a framework whose memory pool must not be bypassed), or
 // code that must never wait on, or fail in, an allocation on a latency path.
-// panda_knn_noalloc serves them.  It runs the same query ordering and the
+// panda_knn_noalloc serves them.  It orders the queries by leaf and runs the
 // same traversal kernel as panda_knn_async, but the ordering's scratch space
 // (query keys, permutation, histogram, error word) is one file-scope device
 // array of fixed size, so the call performs no cudaMalloc, cudaMallocAsync or
 // cudaFree and calls no allocating library routine.  The caller still passes
-// the queries and the output buffers.
+// the queries and the output buffers.  What it leaves out of
+// panda_knn_async's path (no result depends on it): the histogram has at most
+// 2^20 - 1 bins (2^22 there), and dense query sets (2m >= n) keep 32-query
+// packets instead of the job list that gives each warp one bin's queries, so
+// large batches against small trees run somewhat slower than through
+// panda_knn_async.
 //
 // Limits and sharing:
 //   * at most kNoAllocMaxQueries queries per call; larger m is rejected with
@@ -20,7 +25,8 @@
 //     must serialise them (one stream is enough);
 //   * the first call on a device looks up the array's device address
 //     (cudaGetSymbolAddress, once per device with that device current); make
-//     that first call before any stream capture.
+//     that first call before any stream capture.  The address is cached for
+//     the life of the process: it does not survive cudaDeviceReset.
 #include <string.h>
 
 #include <mutex>
@@ -88,10 +94,9 @@ panda_status launch_traversal(const KnnArgs& a, int dp, cudaStream_t s)
 
 using namespace panda;
 
-extern "C" panda_status panda_knn_noalloc(const panda_tree* t, const float* queries, int64_t m, int32_t k,
-                                          int32_t* out_ids, float* out_d2, void* stream)
+static panda_status knn_noalloc_impl(const panda_tree* t, const float* queries, int64_t m, int32_t k,
+                                     int32_t* out_ids, float* out_d2, void* stream)
 {
-    clear_error();
     if (!t || m < 0 || k < 1 || (m > 0 && (!queries || !out_ids || !out_d2))) {
         set_error("panda_knn_noalloc: invalid argument");
         return PANDA_ERR_INVALID_ARGUMENT;
@@ -173,4 +178,16 @@ extern "C" panda_status panda_knn_noalloc(const panda_tree* t, const float* quer
     ka.transpose_max = kTransposeMaxDefault;
     ka.solo = prefer_per_query(m, t->n, t->d);
     return launch_traversal(ka, t->dp, s);
+}
+
+extern "C" panda_status panda_knn_noalloc(const panda_tree* t, const float* queries, int64_t m, int32_t k,
+                                          int32_t* out_ids, float* out_d2, void* stream)
+{
+    clear_error();
+    try {
+        return knn_noalloc_impl(t, queries, m, k, out_ids, out_d2, stream);
+    } catch (...) {   // e.g. std::system_error from the lock: no exception crosses the C ABI
+        set_error("panda_knn_noalloc: host exception");
+        return PANDA_ERR_OUT_OF_MEMORY;
+    }
 }

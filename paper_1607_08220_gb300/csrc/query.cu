@@ -358,6 +358,7 @@ panda_status knn_query(const panda_tree* t, const float* queries, int64_t m, int
     ka.k = k;
     st = launch_knn(ka, t->dp, stream);
     if (st != PANDA_OK) return cleanup(), st;
+    note_tree_use(t, stream);
     timer.end();
     if (host_err) {
         ce = cudaMemcpyAsync(host_err, err, sizeof(unsigned), cudaMemcpyDeviceToHost, stream);
@@ -498,6 +499,7 @@ panda_status knn_self(const panda_tree* t, int32_t k, int32_t* ids, float* d2, c
     ka.d = t->d;
     ka.k = k;
     st = launch_knn(ka, t->dp, stream);
+    if (st == PANDA_OK) note_tree_use(t, stream);
     timer.end();
     if (st == PANDA_OK && host_err) {
         ce = cudaMemcpyAsync(host_err, err, sizeof(unsigned), cudaMemcpyDeviceToHost, stream);

@@ -121,6 +121,8 @@ panda_status panda_refit(panda_tree* t, const float* points, void* stream)
         return PANDA_ERR_INVALID_ARGUMENT;
     }
     cudaStream_t s = (cudaStream_t)stream;
+    // queries still in flight on other streams read the tree: refit starts after them
+    wait_tree_uses(t, s);
     const long long slots = t->node_slots;
     void* scratch = nullptr;
     const size_t bytes = 16 + (size_t)slots * 2 * sizeof(int);

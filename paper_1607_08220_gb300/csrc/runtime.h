@@ -27,6 +27,13 @@ struct panda_tree {
     int32_t depth = 0;
     float root_lo[16] = {0}, root_hi[16] = {0};
     bool pooled = true;       // nodes/points from the stream-ordered pool (cudaMallocAsync)
+    // Work that may still read or write the tree: one event per call that
+    // used it, recorded on that call's stream (completed events are dropped
+    // at the next use).  Freeing the tree waits for these events on the GPU,
+    // not on the host.
+    static constexpr int kMaxUses = 8;
+    cudaEvent_t uses[kMaxUses] = {};
+    int nuses = 0;
 };
 
 namespace panda {
@@ -89,9 +96,18 @@ int64_t launches_so_far();
 panda_status cuda_fail(cudaError_t e, const char* what);
 
 // Stream-ordered allocation from the device's default pool (cached across
-// calls: the pool keeps freed memory for reuse).
+// calls: the pool keeps freed memory for reuse).  The library counts the bytes
+// it holds through these two calls (ws_bytes_held): allocations that are live
+// now, whatever the pool caches.
 panda_status ws_alloc(void** p, size_t bytes, cudaStream_t s, const char* what);
 void ws_free(void* p, cudaStream_t s);
+long long ws_bytes_held();
+
+// Record that work enqueued on stream s uses tree t (reads its tables, or
+// writes them: build, refit).  Thread-safe.
+void note_tree_use(const panda_tree* t, cudaStream_t s);
+// Make stream s wait for every recorded use of t, then forget them.
+void wait_tree_uses(const panda_tree* t, cudaStream_t s);
 
 // Device pointer check: true if p is device memory (or managed) usable by kernels.
 bool is_device_ptr(const void* p);

@@ -667,8 +667,9 @@ def debug_fail_alloc(after: int) -> None:
 
 
 def debug_pool_used() -> int:
-    """Bytes the library holds in the device's stream-ordered pool (the
-    device is synchronised first)."""
+    """Bytes the library holds in the stream-ordered pool right now: its own
+    count of live trees, forests and call workspace (not what the pool caches,
+    nor anyone else's allocations)."""
     v = ctypes.c_int64(0)
     _check(load().panda_debug_pool_used(ctypes.byref(v)))
     return int(v.value)

@@ -6,6 +6,9 @@ identical node by node (split dimension, split value, ranges, boxes, leaf
 order).  Full-size workloads are checked on sampled queries against the
 oracle's exhaustive search plus tree invariants.
 """
+import json
+import os
+
 import numpy as np
 import pytest
 
@@ -105,6 +108,12 @@ def _edge_cases():
         yield f"B{B}", rng.random((5000, 3), dtype=np.float32), rng.random((99, 3), dtype=np.float32), 6, B
     yield "neg_zero", np.array([[-0.0, 1.0], [0.0, 1.0], [0.0, -0.0], [-0.0, 0.0], [1.0, 1.0]] * 20,
                                np.float32), np.array([[0.0, 0.0], [-0.0, 0.5]], np.float32), 7, 4
+    # hand-worked nodes whose split dimension depends on the exact FP32
+    # summation order of the sample variance (tests/golden/variance_order.json)
+    with open(os.path.join(os.path.dirname(__file__), "golden", "variance_order.json")) as f:
+        for node in json.load(f)["nodes"]:
+            pts = np.array(node["points"], np.float32)
+            yield f"variance_{node['name']}", pts, pts[::3].copy(), 5, node["bucket"]
 
 
 @pytest.mark.parametrize("case", list(_edge_cases()), ids=lambda c: c[0])

@@ -1,12 +1,14 @@
 """Served form: requests of different trees, sizes and k coalesced into shared
-launches return exactly what each request returns alone (panda_knn on the
-same tree), a tree can be admitted while requests run, and admission respects
-the memory budget."""
+launches return exactly the CPU oracle's answer for their own tree (ids
+bit-exact, distances to 0 ULP) and exactly what each request returns alone
+(panda_knn on the same tree); a tree can be admitted while requests run, and
+admission respects the memory budget."""
 import threading
 
 import numpy as np
 import pytest
 
+import oracle
 from paper_1607_08220_gb300 import workloads
 
 pytestmark = pytest.mark.gpu
@@ -29,12 +31,25 @@ def alone(P, tree, q, k):
     return ids, d2
 
 
+def assert_oracle(otree, q_np, out):
+    """The served rows against the oracle's Algorithm 1 on the same points."""
+    import torch
+    torch.cuda.synchronize()
+    ei, ed = oracle.knn(otree, q_np, out[0].shape[1])
+    gi, gd = out[0].cpu().numpy(), out[1].cpu().numpy()
+    bad = np.flatnonzero((gi != ei).any(axis=1))
+    assert bad.size == 0, f"{bad.size} rows differ from the oracle, first {bad[:5]}"
+    assert np.array_equal(gd.view(np.uint32), ed.view(np.uint32)), "d2 differ from the oracle"
+
+
 def test_mixed_requests_equal_alone(P):
     import torch
     rng = np.random.default_rng(5)
-    pts_a = torch.from_numpy(workloads.cosmology_points(200_000, seed=50, halos=30)).cuda()
-    pts_b = torch.from_numpy(workloads.plasma_points(150_000, seed=51)).cuda()
-    pts_c = torch.from_numpy(workloads.cosmology_points(30_000, seed=52, halos=5)).cuda()
+    np_a = workloads.cosmology_points(200_000, seed=50, halos=30)
+    np_b = workloads.plasma_points(150_000, seed=51)
+    np_c = workloads.cosmology_points(30_000, seed=52, halos=5)
+    otrees = [oracle.build(x, 32) for x in (np_a, np_b, np_c)]
+    pts_a, pts_b, pts_c = (torch.from_numpy(x).cuda() for x in (np_a, np_b, np_c))
     srv = P.Server(max_batch_queries=40_000)
     tids = [srv.add_tree(pts_a), srv.add_tree(pts_b), srv.add_tree(pts_c)]
     refs = [P.build(pts_a, 32), P.build(pts_b, 32), P.build(pts_c, 32)]
@@ -50,11 +65,12 @@ def test_mixed_requests_equal_alone(P):
         qd = torch.from_numpy(q).cuda()
         out = (torch.empty((m, k), dtype=torch.int32, device="cuda"),
                torch.empty((m, k), dtype=torch.float32, device="cuda"))
-        todo.append((tree, qd, k, out))
+        todo.append((tree, q, qd, k, out))
     torch.cuda.synchronize()
-    reqs = [(srv.submit(tids[tree], qd, k, out), tree, qd, k, out) for tree, qd, k, out in todo]
-    for rid, tree, qd, k, out in reqs:
+    reqs = [(srv.submit(tids[tree], qd, k, out), tree, q, qd, k, out) for tree, q, qd, k, out in todo]
+    for rid, tree, q, qd, k, out in reqs:
         srv.wait(rid, 60)
+        assert_oracle(otrees[tree], q, out)
         ri, rd = alone(P, refs[tree], qd, k)
         assert torch.equal(out[0], ri)
         assert torch.equal(out[1].view(torch.int32), rd.view(torch.int32))
@@ -67,8 +83,10 @@ def test_mixed_requests_equal_alone(P):
 
 def test_tree_admitted_while_requests_run(P):
     import torch
-    pts_a = torch.from_numpy(workloads.cosmology_points(300_000, seed=60, halos=40)).cuda()
-    pts_b = torch.from_numpy(workloads.cosmology_points(250_000, seed=61, halos=40)).cuda()
+    np_a = workloads.cosmology_points(300_000, seed=60, halos=40)
+    np_b = workloads.cosmology_points(250_000, seed=61, halos=40)
+    ot_a, ot_b = oracle.build(np_a, 32), oracle.build(np_b, 32)
+    pts_a, pts_b = torch.from_numpy(np_a).cuda(), torch.from_numpy(np_b).cuda()
     srv = P.Server(max_batch_queries=1 << 20)
     ta = srv.add_tree(pts_a)
     ref_a, ref_b = P.build(pts_a, 32), P.build(pts_b, 32)
@@ -82,17 +100,20 @@ def test_tree_admitted_while_requests_run(P):
     for i in range(30):
         if i == 5:
             th.start()
-        qd = torch.from_numpy(workloads.cosmology_points(20_000, seed=2000 + i, halos=40)).cuda()
+        q = workloads.cosmology_points(20_000, seed=2000 + i, halos=40)
+        qd = torch.from_numpy(q).cuda()
         out = (torch.empty((20_000, 8), dtype=torch.int32, device="cuda"),
                torch.empty((20_000, 8), dtype=torch.float32, device="cuda"))
-        reqs.append((srv.submit(ta, qd, 8, out), ref_a, qd, out))
+        reqs.append((srv.submit(ta, qd, 8, out), ref_a, ot_a, q, qd, out))
     th.join()
-    qd = torch.from_numpy(workloads.cosmology_points(10_000, seed=3000, halos=40)).cuda()
+    q = workloads.cosmology_points(10_000, seed=3000, halos=40)
+    qd = torch.from_numpy(q).cuda()
     out = (torch.empty((10_000, 5), dtype=torch.int32, device="cuda"),
            torch.empty((10_000, 5), dtype=torch.float32, device="cuda"))
-    reqs.append((srv.submit(result["tb"], qd, 5, out), ref_b, qd, out))
-    for rid, ref, qd, out in reqs:
+    reqs.append((srv.submit(result["tb"], qd, 5, out), ref_b, ot_b, q, qd, out))
+    for rid, ref, ot, q, qd, out in reqs:
         srv.wait(rid, 60)
+        assert_oracle(ot, q, out)
         ri, rd = alone(P, ref, qd, out[0].shape[1])
         assert torch.equal(out[0], ri) and torch.equal(out[1].view(torch.int32), rd.view(torch.int32))
     srv.close()
@@ -132,27 +153,31 @@ def test_nonfinite_request_fails_alone(P):
     """A request holding a NaN query fails with PANDA_ERR_NONFINITE_INPUT; the
     requests batched with it still return panda_knn's answers."""
     import torch
-    pts = torch.from_numpy(workloads.cosmology_points(100_000, seed=80, halos=20)).cuda()
+    np_pts = workloads.cosmology_points(100_000, seed=80, halos=20)
+    ot = oracle.build(np_pts, 32)
+    pts = torch.from_numpy(np_pts).cuda()
     srv = P.Server()
     t = srv.add_tree(pts)
     ref = P.build(pts, 32)
     todo = []
     for i in range(12):
-        q = torch.from_numpy(workloads.cosmology_points(3000, seed=900 + i, halos=20)).cuda()
+        qn = workloads.cosmology_points(3000, seed=900 + i, halos=20)
+        q = torch.from_numpy(qn).cuda()
         if i == 5:
             q[17, 1] = float("nan")
         out = (torch.empty((3000, 4), dtype=torch.int32, device="cuda"),
                torch.empty((3000, 4), dtype=torch.float32, device="cuda"))
-        todo.append((q, out))
+        todo.append((qn, q, out))
     torch.cuda.synchronize()
-    rids = [srv.submit(t, q, 4, out) for q, out in todo]
-    for i, (rid, (q, out)) in enumerate(zip(rids, todo)):
+    rids = [srv.submit(t, q, 4, out) for _, q, out in todo]
+    for i, (rid, (qn, q, out)) in enumerate(zip(rids, todo)):
         if i == 5:
             with pytest.raises(P.PandaError) as e:
                 srv.wait(rid, 60)
             assert e.value.status == 2
             continue
         srv.wait(rid, 60)
+        assert_oracle(ot, qn, out)
         ri, rd = alone(P, ref, q, 4)
         assert torch.equal(out[0], ri) and torch.equal(out[1].view(torch.int32), rd.view(torch.int32))
     srv.close()

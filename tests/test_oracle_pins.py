@@ -251,17 +251,93 @@ def test_self_query_rank0(oracle_mod):
     assert np.array_equal(ids[:, 0], np.arange(5000)) and np.all(d2[:, 0] == 0)
 
 
-def test_literal_bound_over_prunes():
-    """Reading C1: Algorithm 1's bound sqrt(d^2 + d'^2) accumulates plane distances
-    along a path; when one dimension is split twice it exceeds the true distance
-    to the region.  1-D: splits at 1 and 2, query at 0, true distance to [2, inf)
-    is 2, the literal bound gives sqrt(1 + 4) = sqrt(5) > 2.2 > 2, so a point at
-    2.1 (distance 2.1 < r' = 2.2) would be pruned."""
-    d_plane1, d_plane2 = 1.0 - 0.0, 2.0 - 0.0
-    literal = math.sqrt(d_plane1 ** 2 + d_plane2 ** 2)
-    true_region_distance = 2.0
-    r_prime = 2.2
-    assert literal > r_prime > 2.1 > true_region_distance
+def test_literal_bound_over_prunes(oracle_mod):
+    """Reading C1, built through the oracle: 1-D points whose tree splits
+    dimension 0 twice on the way to the bucket holding 2.1 (root at s = 1.0,
+    then s = 2.1).  For q = 0 and k = 6, Algorithm 1's accumulated bound for
+    that bucket is sqrt(1.0^2 + 2.1^2) > 2.2, the 6th distance once the other
+    buckets are scanned (the point -2.2), so the literal algorithm would prune
+    it and return -2.2 as the 6th neighbour; the true 6th neighbour is 2.1
+    (distance 2.1 < 2.2).  The oracle's tight-box bound (2.1^2) must visit it."""
+    x = np.array([[-2.2], [-0.5], [0.2], [0.5], [1.0], [1.5], [2.1], [2.5]], np.float32)
+    t = oracle_mod.build(x, 2)
+    e = t.export()
+    # preorder: root, left subtree (3 nodes), right child, its two leaves
+    assert e["split"][0] == np.float32(1.0) and e["dim"][0] == 0
+    right = int(e["right"][0])
+    assert e["split"][right] == np.float32(2.1) and e["dim"][right] == 0
+    far = int(e["right"][right])
+    assert e["leaf"][far] and sorted(e["perm"][e["start"][far]:e["start"][far] + e["count"][far]]) == [6, 7]
+    literal = math.sqrt(float(np.float32(1.0)) ** 2 + float(np.float32(2.1)) ** 2)
+    sixth_without = abs(float(np.float32(-2.2)))
+    assert literal > sixth_without > abs(float(np.float32(2.1)))
+    ids, d2 = oracle_mod.knn(t, np.zeros((1, 1), np.float32), 6)
+    assert ids[0].tolist() == [2, 1, 3, 4, 5, 6]          # 0.2, -0.5, 0.5, 1.0, 1.5, 2.1
+    assert d2[0, 5] == np.float32(np.float32(2.1) * np.float32(2.1))
+    bi, bd = oracle_mod.brute_knn(x, np.zeros((1, 1), np.float32), 6)
+    assert np.array_equal(ids, bi) and np.array_equal(d2.view(np.uint32), bd.view(np.uint32))
+
+
+# ------------------------------------------------------------------ reading R2 (summation order)
+
+
+def _variance_nodes():
+    with open(os.path.join(GOLDEN, "variance_order.json")) as f:
+        return json.load(f)["nodes"]
+
+
+def _root_choice(oracle_mod, node, lib=None):
+    pts = np.array(node["points"], np.float32)
+    e = oracle_mod.build(pts, node["bucket"], lib=lib).export()
+    return int(e["dim"][0]), e
+
+
+@pytest.mark.parametrize("node", _variance_nodes(), ids=lambda n: n["name"])
+def test_variance_order_golden(oracle_mod, node):
+    """Hand-worked nodes (tests/golden/variance_order.json) whose split
+    dimension depends on the exact FP32 summation order of reading R2."""
+    dim, e = _root_choice(oracle_mod, node)
+    assert not e["leaf"][0] and not e["index_split"][0]
+    assert dim == node["dim"]
+    assert e["split"][0] == np.float32(node["split"])
+    assert e["count"][1] == node["left_count"] and e["leaf"][1] and e["leaf"][2]
+    assert e["perm"].tolist() == node["perm"]
+    assert e["lo"].tolist() == node["lo"] and e["hi"].tolist() == node["hi"]
+
+
+# Planted mistakes: the body of the oracle's fixed-order sum replaced by a
+# plausible other order; each must change a golden node's split dimension.
+_SUM_BODY = """    float part[32];
+    for (int p = 0; p < 32; p++) part[p] = 0.0f;
+    for (int64_t j = 0; j < cnt; j++) part[j % 32] = part[j % 32] + vals[j];
+    for (int off = 16; off >= 1; off /= 2)
+        for (int p = 0; p < off; p++) part[p] = part[p] + part[p + off];
+    return part[0];"""
+_MUTANTS = {
+    "sequential": ("""    float acc = 0.0f;
+    for (int64_t j = 0; j < cnt; j++) acc = acc + vals[j];
+    return acc;""", "A_strided_vs_sequential"),
+    "fp64": ("""    double acc = 0.0;
+    for (int64_t j = 0; j < cnt; j++) acc = acc + (double)vals[j];
+    return (float)acc;""", "B_ties_vs_exact"),
+    "partials_in_sequence": ("""    float part[32];
+    for (int p = 0; p < 32; p++) part[p] = 0.0f;
+    for (int64_t j = 0; j < cnt; j++) part[j % 32] = part[j % 32] + vals[j];
+    float acc = 0.0f;
+    for (int p = 0; p < 32; p++) acc = acc + part[p];
+    return acc;""", "A_strided_vs_sequential"),
+}
+
+
+@pytest.mark.parametrize("mutant", sorted(_MUTANTS))
+def test_variance_order_catches_planted_mistakes(oracle_mod, mutant):
+    src = oracle_mod.source_text()
+    assert src.count(_SUM_BODY) == 1, "the oracle's fixed-order sum changed: update this test"
+    body, catcher = _MUTANTS[mutant]
+    lib = oracle_mod.compile_variant(src.replace(_SUM_BODY, body), mutant)
+    nodes = {n["name"]: n for n in _variance_nodes()}
+    dim, _ = _root_choice(oracle_mod, nodes[catcher], lib=lib)
+    assert dim != nodes[catcher]["dim"], f"a {mutant} sum was not caught by {catcher}"
 
 
 # ------------------------------------------------------------------ radius-bounded KNN (Algorithm 1's r)

@@ -8,7 +8,15 @@ the call) and leave the library usable; once the injection point lies past
 the call's last allocation the call succeeds with the same result as without
 injection.  No GPU fault is involved: the failure is made on the host.  The
 file runs after the other GPU tests (its name), so that a failure here stops
-none of them under -x."""
+none of them under -x (only the allocation-free entry point's test comes later).
+
+The byte count is the library's own count of its live allocations
+(panda_debug_pool_used), and the garbage collector is off during a sweep:
+a tree that an earlier test left to the collector would otherwise be freed
+in the middle of a sweep and lower the count by memory the swept call never
+held."""
+import gc
+
 import numpy as np
 import pytest
 
@@ -34,7 +42,10 @@ def sweep(P, call, max_allocs=128):
     """Fail allocation 0, 1, 2, ... of `call` until it succeeds; returns its
     result and how many allocations it made."""
     import torch
+    gc.collect()
     torch.cuda.synchronize()
+    was_enabled = gc.isenabled()
+    gc.disable()
     base = P.debug_pool_used()
     try:
         for j in range(max_allocs):
@@ -51,6 +62,8 @@ def sweep(P, call, max_allocs=128):
         raise AssertionError(f"still failing after {max_allocs} injected failures")
     finally:
         P.debug_fail_alloc(-1)
+        if was_enabled:
+            gc.enable()
 
 
 def same(a, b):
