@@ -57,6 +57,8 @@ def parse():
                          "general: panda_knn with the query buffer; auto: self when it applies")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the served (plasma stream) and batched (512 sets) measurements of the default run")
     ap.add_argument("--n", type=int, default=0, help="override n of cosmology_self (profiling runs)")
     return ap.parse_args()
 
@@ -148,8 +150,9 @@ class ClockSampler:
 
 
 def cpu_oracle_step(pts, k, bucket, sample=CPU_SAMPLE):
-    """One bounded oracle step: build over the first `sample` points (a uniform
-    subsample: the workload rows are shuffled) and answer their self-queries."""
+    """One bounded oracle step (the reference arm): build over the first
+    `sample` points (a uniform subsample: the workload rows are shuffled) and
+    answer their self-queries."""
     import oracle
     sub = np.ascontiguousarray(pts[:sample])
     t0 = time.perf_counter()
@@ -158,6 +161,29 @@ def cpu_oracle_step(pts, k, bucket, sample=CPU_SAMPLE):
     oracle.knn(tree, sub, k, threads=0)
     t2 = time.perf_counter()
     return sub.shape[0], t1 - t0, t2 - t1
+
+
+ONE_THREAD_QUERIES = 1 << 16
+
+
+def oracle_full(points, queries, k, bucket):
+    """The oracle on the benchmark's own inputs: its build over all n points
+    (single-threaded, as written), its Algorithm 1 over all m queries on every
+    host core with the per-query visit counts (the algorithmic work of the
+    roofline), and the same query on one thread over a sample of the queries."""
+    import oracle
+    t0 = time.perf_counter()
+    tree = oracle.build(points, bucket)
+    t1 = time.perf_counter()
+    _, _, vis = oracle.knn(tree, queries, k, threads=0, visits=True)
+    t2 = time.perf_counter()
+    sample = np.ascontiguousarray(queries[:ONE_THREAD_QUERIES])
+    t3 = time.perf_counter()
+    oracle.knn(tree, sample, k, threads=1)
+    t4 = time.perf_counter()
+    v = vis.sum(axis=0)
+    return {"build_s": t1 - t0, "query_s": t2 - t1, "query1_s": t4 - t3, "query1_m": sample.shape[0],
+            "visit_nodes": int(v[0]), "visit_points": int(v[1]), "depth": tree.depth}
 
 
 def cpu_cores():
@@ -178,13 +204,15 @@ def cpu_model():
     return "unknown"
 
 
-def cpu_baseline_obj(pts, k, bucket):
-    n, tb, tq = cpu_oracle_step(pts, k, bucket)
-    return {"value": n / (tb + tq), "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
-            "cpu": cpu_model(),
-            "sample": f"oracle build (1 thread) + self-KNN (OpenMP, all cores) of the first {n} of "
-                      f"the {pts.shape[0]} workload points (same distribution), k={k}, B={bucket}",
-            "build_pts_per_s": n / tb, "query_per_s": n / tq, "build_s": tb, "query_s": tq}
+def cpu_baseline_obj(points, queries, k, bucket, full):
+    n, m = points.shape[0], queries.shape[0]
+    tb, tq = full["build_s"], full["query_s"]
+    return {"value": m / (tb + tq), "unit": UNIT, "cores": cpu_cores(), "kind": "oracle", "cpu": cpu_model(),
+            "sample": f"the full workload: oracle build over all {n} points (1 thread) + Algorithm 1 for all "
+                      f"{m} queries (OpenMP, all cores), k={k}, B={bucket}; the 1-thread query rate is "
+                      f"timed on the first {full['query1_m']} queries",
+            "build_pts_per_s": n / tb, "query_per_s": m / tq, "query_per_s_1thread": full["query1_m"] / full["query1_s"],
+            "build_s": tb, "query_s": tq}
 
 
 def run_reference(args):
@@ -224,13 +252,24 @@ def run_reference(args):
 
 # DRAM traffic of the packet traversal kernel (k_knn, d = 3, k = 10, all-points
 # query) per query: dram__bytes_read.sum + dram__bytes_write.sum of one ncu
-# capture on the cosmology self-KNN at n = m = 2^23 (1.177537 GB + 1.490322 GB),
-# scaled to a full launch by the number of queries.  It describes the kernel as
-# committed with profiles/k_knn_cosmology_n8388608.md and must be re-captured
-# (or dropped) whenever that kernel changes.
+# capture on the cosmology self-KNN at n = m = 2^23, scaled to a full launch by
+# the number of queries.  It describes the kernel sources whose SHA-1 is
+# `kernel_sha1`; once they change, the figure is dropped (traffic: null) until
+# the committed ncu capture is taken again.
 KNN_TRAFFIC = {"workload": "cosmology_self", "path": "self", "d": 3, "k": 10,
                "bytes_per_query": (1.177537e9 + 1.490322e9) / 2 ** 23,
-               "source": "ncu capture at n = m = 2^23, scaled by queries (profiles/k_knn_cosmology_n8388608.md)"}
+               "kernel_sha1": "",
+               "source": "one ncu capture of k_knn at n = m = 2^23 (cosmology self-KNN), scaled by queries"}
+KNN_SOURCES = ("query.cuh", "knn_launch.cuh", "common.cuh")
+
+
+def knn_sources_sha1() -> str:
+    import hashlib
+    h = hashlib.sha1()
+    for name in KNN_SOURCES:
+        with open(os.path.join(ROOT, "paper_1607_08220_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
 
 
 def max_over_ranks(x: float, world: int, device: str) -> float:
@@ -439,6 +478,12 @@ def run_ours(args):
                "d2h_bytes_per_step": int(m * k * 8), "ms_per_step": e_ms / args.steps,
                "path": "blocking calls, one step after the other"}
 
+    # ---- the oracle on the same inputs (rank 0 at N = 1): the CPU baseline,
+    # and its visit counts as the traversal's algorithmic work
+    full = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        full = oracle_full(w.points, w.queries, k, B)
+
     # ---- roofline of the dominant kernel (outside the timed region: work counts)
     peaks, peak_src = load_peaks()
     per_step = {nm: (v[0] / args.steps, v[1] / args.steps) for nm, v in phases.items()}
@@ -453,21 +498,33 @@ def run_ours(args):
         _, _, vis, kstats = P.knn_visits(t, None if use_self else q_dev, k, order=args.order)
         torch.cuda.synchronize()
         v = vis.to(torch.int64).sum(dim=0).cpu().numpy()
-        flops = 3.0 * d * float(v[0] + v[1])
+        if full is not None:
+            vn, vp = full["visit_nodes"], full["visit_points"]
+            work_src = ("the oracle's Algorithm 1 on the same tree (identical node by node): nodes processed "
+                        "and bucket points scanned, summed over all queries")
+        else:
+            vn, vp = int(v[0]), int(v[1])
+            work_src = "the kernel's own per-query counts (the oracle leg did not run: N > 1 or --no-cpu-baseline)"
+        flops = 3.0 * d * float(vn + vp)
         sms = torch.cuda.get_device_properties(0).multi_processor_count
         peak = sms * 128 * sm_max * 1e6 / 1e12
         achieved = flops / (dom_ms / 1e3) / 1e12
-        traffic = None
+        traffic, traffic_src = None, None
         if (args.workload == KNN_TRAFFIC["workload"] and use_self and d == KNN_TRAFFIC["d"]
                 and k == KNN_TRAFFIC["k"]):
-            traffic = KNN_TRAFFIC["bytes_per_query"] * m
+            if knn_sources_sha1() == KNN_TRAFFIC["kernel_sha1"]:
+                traffic = KNN_TRAFFIC["bytes_per_query"] * m
+                traffic_src = KNN_TRAFFIC["source"]
+            else:
+                traffic_src = "null: the kernel sources changed since the last ncu capture"
         roof = {"kernel": kernel_phases[dom], "bound": "alu", "achieved": achieved, "peak": peak,
-                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
-                "traffic_source": KNN_TRAFFIC["source"] if traffic is not None else None,
-                "algorithmic": f"3*d FP32 ops (sub, mul, add) per needed node box and per scanned bucket "
-                               f"point: nodes={int(v[0])} points={int(v[1])} per launch",
+                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic, "traffic_source": traffic_src,
+                "algorithmic": f"3*d FP32 ops (sub, mul, add) per visited node's box and per scanned bucket "
+                               f"point: nodes={vn} points={vp} per launch",
+                "algorithmic_source": work_src,
                 "peak_source": f"{sms} SMs x 128 FP32 lanes x {sm_max:.0f} MHz (derived)",
-                "ms_per_launch": dom_ms / max(dom_launches, 1), "events": kstats}
+                "ms_per_launch": dom_ms / max(dom_launches, 1),
+                "kernel_counters": {"needed_nodes": int(v[0]), "needed_points": int(v[1]), **kstats}}
     # the build's streaming kernels against the HBM roofline (per step, all their launches)
     exp = t.export()
     act = level_active_points(exp, info["subtree_threshold"])
@@ -491,9 +548,31 @@ def run_ours(args):
                          else f"of {peak_src}")
     t.free()
 
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline_obj(w.points, k, B)
+    cpu = cpu_baseline_obj(w.points, w.queries, k, B, full) if full is not None else None
+    del ids, d2
+    torch.cuda.empty_cache()
+
+    # ---- the metric's other half: the served and batched forms against the
+    # plain one-request-per-launch path (rank 0 at N = 1)
+    forms = {}
+    if rank == 0 and world == 1 and not args.no_forms and args.workload == "cosmology_self":
+        r = measure_served(args, "plasma_serving")
+        sv, pl = r["served"], r["plain"]
+        forms["served"] = {
+            "workload": r["config"]["workload"], "requests": r["config"]["requests"],
+            "queries": r["config"]["queries"], "value": sv["value"], "unit": UNIT,
+            "p50_ms": sv["p50_ms"], "p99_ms": sv["p99_ms"], "batches": sv["batches"],
+            "plain": {"value": pl["value"], "p50_ms": pl["p50_ms"], "p99_ms": pl["p99_ms"], "path": pl["path"]},
+            "capacity": {"served": sv["burst_value"], "plain": pl["burst_value"],
+                         "speedup": r["speedup_vs_plain"], "note": r["speedup_note"]},
+            "rate_sweep": sv["rate_sweep"], "slo_p99_ms": sv["slo_p99_ms"],
+            "sustained_requests_per_s": sv["sustained_requests_per_s"],
+            "identical_to_plain": r["identical_to_plain"], "clocks": r["clocks"],
+            "first_tree_build_s": r["first_tree_build_s"],
+            "second_tree_admit_build_s": r["second_tree_admit_build_s"]}
+        torch.cuda.empty_cache()
+        forms["batched"] = measure_batched(args)
+        torch.cuda.empty_cache()
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": max(3, args.warmup), "ms_per_step": ms_per_step, "higher_is_better": True,
@@ -508,7 +587,8 @@ def run_ours(args):
             "phases_ms_per_step": {nm: round(v[0], 4) for nm, v in per_step.items()},
             "build_roofline": {"peak": hbm_peak, "unit": "GB/s", "peak_source": f"{peak_src} STREAM-style copy",
                                "kernels": build_roof},
-            "tree": {"nodes": info["num_nodes"], "leaves": info["num_leaves"], "depth": info["depth"]}}
+            "tree": {"nodes": info["num_nodes"], "leaves": info["num_leaves"], "depth": info["depth"]},
+            **forms}
     if classify:
         acc = float((pred.cpu().numpy() == rule_labels(w.queries)).mean())
         line["classification"] = {"rule": "label = min((x0 > 0) + 2 (x1 > 0.2), 2) on the 10-D features",
@@ -522,15 +602,31 @@ def run_ours(args):
 
 
 def run_batched(args):
+    """Batched form on its own JSON line (--workload batched_sets)."""
+    import torch
+
+    import paper_1607_08220_gb300 as P
+    from paper_1607_08220_gb300 import build_ext
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    build_ext.build()
+    P.load()
+    res = measure_batched(args)
+    line = {"metric": METRIC + " [batched form]", "value": res["value"], "unit": UNIT,
+            "n_gpus": 1, "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": res["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "config": res.pop("config"), "clocks": res.pop("clocks"),
+            "gpu_launches": res.pop("gpu_launches"), **res}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def measure_batched(args):
     """Batched form: all sets built and queried by one captured graph, against the
     plain path (one panda_build + panda_knn per set, serialised on one stream)."""
     import torch
 
     import paper_1607_08220_gb300 as P
-    from paper_1607_08220_gb300 import build_ext, workloads
-    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-    build_ext.build()
-    P.load()
+    from paper_1607_08220_gb300 import workloads
     t0 = time.time()
     sets = workloads.batched_sets(nsets=args.nsets)
     gen_s = time.time() - t0
@@ -591,24 +687,20 @@ def run_batched(args):
                torch.equal(outs[i][1].view(torch.int32), batch.result(i)[1].view(torch.int32))
                for i in range(len(sets)) if nq[i])
     info = batch.info()
-    line = {"metric": METRIC + " [batched form]", "value": m_total / (b_ms / 1e3), "unit": UNIT,
-            "n_gpus": 1, "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": b_ms,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-            "data": "synthetic",
-            "config": {"workload": f"batched_sets: {len(sets)} sets, sizes log-uniform [1e3, 2e6], "
-                                   f"{sum(npts)} points, {m_total} queries, k in {{4,8,16,32}}, "
-                                   f"B={tuned['bucket']} (autotuned)",
-                       "sets": len(sets), "points": int(sum(npts)), "queries": int(m_total),
-                       "step": "build every set's tree + answer every set's queries (one graph launch)",
-                       "l2": "inputs larger than L2"},
-            "clocks": clk, "gpu_launches": int(info["kernels_per_run"]) * args.steps,
-            "plain": {"value": m_total / (p_ms / 1e3), "ms_per_step": p_ms,
-                      "path": "one panda_build + one panda_knn per set, serialised on one stream"},
-            "speedup_vs_plain": p_ms / b_ms, "identical_to_plain": bool(same), "autotuned": tuned,
-            "build_pts_per_s": sum(npts) / (b_ms / 1e3), "generation_s": gen_s}
-    print(json.dumps(line), flush=True)
+    res = {"value": m_total / (b_ms / 1e3), "unit": UNIT, "ms_per_step": b_ms, "steps": args.steps,
+           "config": {"workload": f"batched_sets: {len(sets)} sets, sizes log-uniform [1e3, 2e6], "
+                                  f"{sum(npts)} points, {m_total} queries, k in {{4,8,16,32}}, "
+                                  f"B={tuned['bucket']} (autotuned)",
+                      "sets": len(sets), "points": int(sum(npts)), "queries": int(m_total),
+                      "step": "build every set's tree + answer every set's queries (one graph launch)",
+                      "l2": "inputs larger than L2"},
+           "clocks": clk, "gpu_launches": int(info["kernels_per_run"]) * args.steps,
+           "plain": {"value": m_total / (p_ms / 1e3), "ms_per_step": p_ms,
+                     "path": "one panda_build + one panda_knn per set, serialised on one stream"},
+           "speedup_vs_plain": p_ms / b_ms, "identical_to_plain": bool(same), "autotuned": tuned,
+           "build_pts_per_s": sum(npts) / (b_ms / 1e3), "generation_s": gen_s}
     batch.free()
-    return 0
+    return res
 
 
 def _latency_stats(lat_ms):
@@ -618,6 +710,24 @@ def _latency_stats(lat_ms):
 
 
 def run_served(args):
+    """Served form on its own JSON line (--workload plasma_serving / features_10d_served)."""
+    import torch
+
+    import paper_1607_08220_gb300 as P
+    from paper_1607_08220_gb300 import build_ext
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    build_ext.build()
+    P.load()
+    res = measure_served(args, args.workload)
+    line = {"metric": METRIC + " [served form]", "value": res["value"], "unit": UNIT, "n_gpus": 1,
+            "steps": 1, "warmup": 0, "ms_per_step": res["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": res.pop("config"), "clocks": res.pop("clocks"), **res}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def measure_served(args, which: str):
     """Served form on a Poisson request stream vs the plain path (one panda_knn
     per request, in arrival order, one at a time)."""
     import threading
@@ -625,12 +735,9 @@ def run_served(args):
     import torch
 
     import paper_1607_08220_gb300 as P
-    from paper_1607_08220_gb300 import build_ext, workloads
-    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-    build_ext.build()
-    P.load()
+    from paper_1607_08220_gb300 import workloads
     t_gen = time.time()
-    if args.workload == "plasma_serving":
+    if which == "plasma_serving":
         trees_np = [workloads.plasma_points(100_000_000, seed=0)]
         second = workloads.plasma_points(20_000_000, seed=4)
         reqs = workloads.plasma_requests(duration_s=args.duration)
@@ -764,9 +871,9 @@ def run_served(args):
                                                                    ref[i][1].view(torch.int32))
                for i in range(len(reqs)))
     srv.close()
-    line = {"metric": METRIC + " [served form]", "value": served["value"], "unit": UNIT, "n_gpus": 1,
-            "steps": 1, "warmup": 0, "ms_per_step": span_s * 1e3, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+    for t in plain_trees:
+        t.free()
+    return {"value": served["value"], "unit": UNIT, "ms_per_step": span_s * 1e3,
             "config": {"workload": desc, "requests": len(reqs), "queries": int(m_total),
                        "l2": "inputs larger than L2"},
             "clocks": clk, "served": served, "plain": plain,
@@ -774,8 +881,6 @@ def run_served(args):
             "speedup_note": "capacity (all requests submitted at once), served vs plain",
             "identical_to_plain": bool(same), "first_tree_build_s": build_first_s,
             "second_tree_admit_build_s": admit_info.get("build_s"), "generation_s": gen_s}
-    print(json.dumps(line), flush=True)
-    return 0
 
 
 def run_refit(args):
