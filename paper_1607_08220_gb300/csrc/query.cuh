@@ -135,6 +135,34 @@ __device__ __forceinline__ void heap_replace_root(unsigned long long* h, int k, 
     h[i * kKnnThreads] = c;
 }
 
+// The packet traversal's DFS stack (Algorithm 1's S) is the same for every lane
+// of the warp, so it is held once, spread over the warp's registers: entry j
+// lives in lane (j mod 32)'s slot j / 32.  A push writes one lane's slot, a
+// pop reads the top entry back with one shuffle; no local memory is involved.
+// Algorithm 1 pushes the far child and then the near child and pops the near
+// child at once; the traversal keeps the near child as its next node instead
+// and pushes only the far one (the same visit order), so the stack holds at
+// most one far sibling per level above the current node: 64 entries cover the
+// deepest valid tree (an inner node lies above depth kMaxDepth).
+struct WarpStack {
+    int s0 = 0, s1 = 0;
+    static constexpr int kCap = 64;
+    __device__ __forceinline__ void push(int& sp, int v, int lane)
+    {
+        if (lane == (sp & 31)) {
+            if (sp & 32) s1 = v;
+            else s0 = v;
+        }
+        sp++;
+    }
+    __device__ __forceinline__ int pop(int& sp) const
+    {
+        sp--;
+        return __shfl_sync(kFull, (sp & 32) ? s1 : s0, sp & 31);
+    }
+};
+static_assert(WarpStack::kCap >= kMaxDepth, "warp stack too small for the deepest tree");
+
 // Squared distance from q to the tight box of a node record (dims in order, unfused).
 template <int DP>
 __device__ __forceinline__ float record_box_d2(const float4* rec, const float (&q)[DP])
@@ -169,22 +197,28 @@ __device__ __forceinline__ void knn_lane_solo(const KnnArgs& a, const KnnSet& S,
 {
     constexpr int NV = (DP + 1 + 3) / 4;
     constexpr int NS = (4 + 2 * DP + 3) / 4;
-    int stn[kMaxDepth + 4];
-    float stb[kMaxDepth + 4];
+    // Far children wait on the lane's stack with their bounds; the near child
+    // is the next node at once (Algorithm 1 pushes it last and pops it first),
+    // so the stack holds at most one entry per level above the current node.
+    int stn[kMaxDepth];
+    float stb[kMaxDepth];
     int sp = 0;
-    stn[sp] = S.root;
-    stb[sp] = 0.0f;
-    sp++;
+    int node = S.root;
+    float nb = 0.0f;   // bound of `node`
     long long budget = 2LL * S.num_nodes + 8;
-    while (sp > 0) {
+    for (;;) {
         if (--budget < 0) {
             atomicOr(a.err, kErrInternal);
             break;
         }
-        sp--;
-        const int node = stn[sp];
         const float kd = __uint_as_float((unsigned)(kth >> 32));
-        if (stb[sp] > kd) continue;
+        if (nb > kd) {              // pruned: the next waiting far child
+            if (sp == 0) break;
+            sp--;
+            node = stn[sp];
+            nb = stb[sp];
+            continue;
+        }
         if ((unsigned)node >= (unsigned)S.num_nodes) {
             atomicOr(a.err, kErrInternal);
             break;
@@ -222,9 +256,13 @@ __device__ __forceinline__ void knn_lane_solo(const KnnArgs& a, const KnnSet& S,
                     kth = RAD ? min(h[0], a.rkey) : h[0];
                 }
             }
+            if (sp == 0) break;
+            sp--;
+            node = stn[sp];
+            nb = stb[sp];
         } else {
             const int c0 = hd.x;
-            if ((unsigned)(c0 + 1) >= (unsigned)S.num_nodes || sp + 2 > kMaxDepth + 4) {
+            if ((unsigned)(c0 + 1) >= (unsigned)S.num_nodes || sp >= kMaxDepth) {
                 atomicOr(a.err, kErrInternal);
                 break;
             }
@@ -238,13 +276,12 @@ __device__ __forceinline__ void knn_lane_solo(const KnnArgs& a, const KnnSet& S,
             const bool right_near = qd >= __int_as_float(hd.z);
             const float bn = right_near ? b1 : b0, bf = right_near ? b0 : b1;
             if (bf <= kd) {
-                stn[sp] = right_near ? c0 : c0 + 1;   // far child first
+                stn[sp] = right_near ? c0 : c0 + 1;   // far child waits
                 stb[sp] = bf;
                 sp++;
             }
-            stn[sp] = right_near ? c0 + 1 : c0;       // near child last
-            stb[sp] = bn;
-            sp++;
+            node = right_near ? c0 + 1 : c0;          // near child next
+            nb = bn;
         }
     }
 }
@@ -321,18 +358,17 @@ __device__ __forceinline__ void knn_warp_job(const KnnArgs& a, const KnnSet& S, 
     if (SOLO_OK && S.solo) {
         if (valid) knn_lane_solo<DP, RAD>(a, S, q, h, K, kth, vnodes, vpts);
     } else {
-    int stack[kMaxDepth + 4];
+    WarpStack stack;
     int sp = 0;
-    stack[sp++] = S.root;
-    // A valid tree is visited in at most 2 * num_nodes pops; the cap only
+    int node = S.root;
+    // A valid tree is visited in at most 2 * num_nodes steps; the cap only
     // guarantees termination (with an error flag) should a node table be corrupt.
-    long long budget = 2LL * S.num_nodes + 8;
-    while (sp > 0) {
-        if (--budget < 0 || (unsigned)stack[sp - 1] >= (unsigned)S.num_nodes) {
+    unsigned budget = (unsigned)min(S.num_nodes + 8, 0xffffffffLL);
+    for (;;) {
+        if (budget-- == 0 || (unsigned)node >= (unsigned)S.num_nodes) {
             if (lane == 0) atomicOr(a.err, kErrInternal);
             break;
         }
-        const int node = stack[--sp];
         const float4* rec = S.nodes + (long long)node * NS;
         float f[4 * NS];
 #pragma unroll
@@ -355,6 +391,8 @@ __device__ __forceinline__ void knn_warp_job(const KnnArgs& a, const KnnSet& S, 
         const unsigned needm = __ballot_sync(kFull, need);
         if (!needm) {
             if (stats) st[7]++;
+            if (sp == 0) break;       // nothing left on the stack: done
+            node = stack.pop(sp);
             continue;
         }
         if (STATS) vnodes += need;
@@ -484,15 +522,24 @@ __device__ __forceinline__ void knn_warp_job(const KnnArgs& a, const KnnSet& S, 
 #pragma unroll
             for (int k = 0; k < DP; k++)
                 if (k == dim) qd = q[k];
-            const unsigned br = __ballot_sync(kFull, need && qd >= sv);
+            const bool right_side = qd >= sv;
+            const unsigned br = __ballot_sync(kFull, need && right_side);
             const bool right_near = 2 * __popc(br) >= __popc(needm);
-            if (sp + 2 > kMaxDepth + 4) {
+            if (sp >= WarpStack::kCap) {
                 if (lane == 0) atomicOr(a.err, kErrInternal);
                 break;
             }
-            stack[sp++] = h0 + (right_near ? 0 : 1);   // far child first
-            stack[sp++] = h0 + (right_near ? 1 : 0);   // near child last
+            // a lane on the near side needs the far child only if the split
+            // plane lies within its k-th distance (the far box lies beyond it)
+            const float pg = __fsub_rn(qd, sv);
+            const bool far_need = need && ((meta & kMetaIndex) || right_side != right_near ||
+                                           !(__fmul_rn(pg, pg) > kd));
+            if (__any_sync(kFull, far_need)) stack.push(sp, h0 + (right_near ? 0 : 1), lane);
+            node = h0 + (right_near ? 1 : 0);                   // near child next
+            continue;
         }
+        if (sp == 0) break;   // a bucket was the last node: the traversal is complete
+        node = stack.pop(sp);
     }
     }   // packet traversal
     __syncwarp();
@@ -531,16 +578,16 @@ __device__ __forceinline__ void knn_warp_job(const KnnArgs& a, const KnnSet& S, 
 
 
 // Resident blocks per SM the register allocation must allow.  The one-set
-// packet traversal at low dimension fits 32 registers with a few bytes of
-// spill and then runs at full occupancy (measured 8% faster on 3-D self-KNN
-// than at 45 registers and 10 blocks); wider points keep about 48 registers.
+// packet traversal at low dimension runs at 12 blocks (40 registers, no
+// spill; 2^24 3-D self-KNN 10.28 ms against 10.31 ms at 16 blocks and 32
+// registers, which spill a few values); wider points keep about 48 registers.
 // The request lookup and the job queue hold a few more values; kernels with
 // the per-query traversal keep 64 registers (its per-lane stacks).
 constexpr int knn_min_blocks(int dp, int mode, bool solo)
 {
     return (solo || mode == kKnnManySets || mode == kKnnStats) ? 8
            : mode == kKnnOneTreeReqs                          ? (dp <= 4 ? 12 : 8)
-                                                              : (dp <= 4 ? 16 : 10);
+                                                              : (dp <= 4 ? 12 : 10);
 }
 
 // MODE kKnnOneSet / kKnnOneTreeReqs: one tree, warp w takes positions
