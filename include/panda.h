@@ -353,10 +353,13 @@ panda_status panda_tree_save(const panda_tree* tree, const char* path);
 panda_status panda_tree_load(const char* path, panda_tree** out);
 
 /* ---- diagnostics --------------------------------------------------------------
- * Phase timing: when enabled, the library records CUDA events on the launching
- * stream around each phase of the next builds/queries.  panda_phase_times
- * writes up to `cap` (name, milliseconds, launches) triples of the last call
- * that finished on this thread and returns how many there were. */
+ * Phase timing: enable = 1 records CUDA events on the launching stream around
+ * each phase of the next builds/queries; enable = 2 records only the
+ * traversal phase ("query.traverse"), so no event separates the other kernels
+ * (consecutive kernels then overlap their launches: programmatic dependent
+ * launch); 0 turns it off.  panda_phase_times writes up to `cap` (name,
+ * milliseconds, launches) triples of the last call that finished on this
+ * thread and returns how many there were. */
 void panda_set_phase_timing(int32_t enable);
 int32_t panda_phase_times(const char** names, float* ms, int32_t* launches, int32_t cap);
 /* Same as panda_knn_async (queries NULL and m = the tree's n: the all-points

@@ -19,7 +19,7 @@ namespace panda {
 namespace {
 thread_local char g_err[512] = "";
 thread_local int64_t g_launches = 0;
-bool g_timing = false;
+int g_timing = 0;   // 0 off, 1 every phase, 2 the traversal phase only
 thread_local bool g_timing_suppressed = false;
 
 struct PhaseRow {
@@ -68,10 +68,10 @@ panda_status note_launch(const char* what)
 }
 
 int64_t launches_so_far() { return g_launches; }
-bool phase_timing_enabled() { return g_timing; }
+bool phase_timing_enabled() { return g_timing != 0; }
 void set_phase_timing_suppressed(bool on) { g_timing_suppressed = on; }
 
-PhaseTimer::PhaseTimer(cudaStream_t s) : stream_(s), on_(g_timing && !g_timing_suppressed) {}
+PhaseTimer::PhaseTimer(cudaStream_t s) : stream_(s), on_(g_timing != 0 && !g_timing_suppressed) {}
 
 PhaseTimer::~PhaseTimer()
 {
@@ -94,7 +94,12 @@ void PhaseTimer::mark(const char* name)
 
 void PhaseTimer::begin(const char* name)
 {
-    if (on_) mark(name);
+    if (!on_) return;
+    if (g_timing == 2 && strcmp(name, "query.traverse") != 0) {
+        end();   // traversal-only mode: no event between the other kernels
+        return;
+    }
+    mark(name);
 }
 
 void PhaseTimer::end()
@@ -307,7 +312,7 @@ const char* panda_status_string(panda_status s)
 
 const char* panda_last_error(void) { return g_err; }
 
-void panda_set_phase_timing(int32_t enable) { g_timing = enable != 0; }
+void panda_set_phase_timing(int32_t enable) { g_timing = enable == 2 ? 2 : (enable != 0 ? 1 : 0); }
 
 int32_t panda_phase_times(const char** names, float* ms, int32_t* launches, int32_t cap)
 {

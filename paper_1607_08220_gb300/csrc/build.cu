@@ -80,6 +80,7 @@ __device__ __forceinline__ bool finite_bits(float v)
 
 __global__ void k_transpose(BuildArgs a)
 {
+    griddep_enter();
     const long long stride = (long long)gridDim.x * blockDim.x;
     bool bad = false;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < a.n_pad; i += stride) {
@@ -127,11 +128,17 @@ constexpr int kPlanPer = 4;   // consecutive active nodes per thread in one pass
 
 __device__ void block_plan_tiles(BuildArgs& a, int x, int A)
 {
+    // Nodes cut into more than kOwnTiles tiles (the top levels: a few nodes of
+    // many tiles each) have their tile records written by the whole block; the
+    // thread that owns a node writes the others.
+    constexpr int kOwnTiles = 8, kBigCap = 1024;
     __shared__ int sh[33];
-    __shared__ int base;
+    __shared__ int base, nbig;
+    __shared__ int big_node[kBigCap], big_off[kBigCap], big_cnt[kBigCap];
     if (threadIdx.x == 0) base = 0;
     __syncthreads();
     for (int c = 0; c < A; c += blockDim.x * kPlanPer) {
+        if (threadIdx.x == 0) nbig = 0;
         const int a0 = c + threadIdx.x * kPlanPer;
         int nt[kPlanPer], sum = 0;
 #pragma unroll
@@ -144,15 +151,25 @@ __device__ void block_plan_tiles(BuildArgs& a, int x, int A)
             sum += nt[r];
         }
         int tot;
-        int off = block_excl_scan(sum, sh, &tot) + base;
+        int off = block_excl_scan(sum, sh, &tot) + base;   // (its barriers also order nbig = 0)
 #pragma unroll
         for (int r = 0; r < kPlanPer; r++) {
             const int ai = a0 + r;
             if (ai >= A) break;
-            const Active nd = a.act[x][ai];
             a.tile_base[x][ai] = off;
+            int j0 = 0;
+            if (nt[r] > kOwnTiles) {
+                const int slot = atomicAdd(&nbig, 1);
+                if (slot < kBigCap) {
+                    big_node[slot] = ai;
+                    big_off[slot] = off;
+                    big_cnt[slot] = nt[r];
+                    j0 = nt[r];   // written below by the block
+                }
+            }
+            const Active nd = a.act[x][ai];
             const int first = nd.start / kTile;
-            for (int j = 0; j < nt[r]; j++) {
+            for (int j = j0; j < nt[r]; j++) {
                 if (off + j >= a.tile_cap) { atomicOr(a.err, kErrTileOverflow); break; }
                 Tile t;
                 t.node = ai;
@@ -162,6 +179,22 @@ __device__ void block_plan_tiles(BuildArgs& a, int x, int A)
                 a.tiles[x][off + j] = t;
             }
             off += nt[r];
+        }
+        __syncthreads();
+        const int nb = min(nbig, kBigCap);
+        for (int e = 0; e < nb; e++) {
+            const int ai = big_node[e], o = big_off[e], cnt = big_cnt[e];
+            const Active nd = a.act[x][ai];
+            const int first = nd.start / kTile;
+            for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
+                if (o + j >= a.tile_cap) { atomicOr(a.err, kErrTileOverflow); break; }
+                Tile t;
+                t.node = ai;
+                t.begin = max(nd.start, (first + j) * kTile);
+                t.end = min(nd.start + nd.count, (first + j + 1) * kTile);
+                t.first = (j == 0);
+                a.tiles[x][o + j] = t;
+            }
         }
         __syncthreads();
         if (threadIdx.x == 0) base += tot;
@@ -178,6 +211,7 @@ __device__ void block_plan_tiles(BuildArgs& a, int x, int A)
 // subtree stage.
 __global__ void k_init(BuildArgs a)
 {
+    griddep_enter();
     __shared__ int sh[33];
     __shared__ int s_act, s_small;
     const int nsets = a.set_off ? a.nsets : 1;
@@ -241,6 +275,7 @@ __global__ void k_init(BuildArgs a)
 // active would have needed more passes; report it instead of building them.
 __global__ void k_check_levels(BuildArgs a, int L)
 {
+    griddep_enter();
     if (threadIdx.x == 0 && a.cnt[kCntActive0 + (L & 1)] > 0) atomicOr(a.err, kErrLevels);
 }
 
@@ -252,6 +287,7 @@ constexpr int kSampleThreads = 256;   // k_sample's block (8 warps over 1024 sam
 
 __global__ void __launch_bounds__(kSampleThreads) k_sample(BuildArgs a, int L)
 {
+    griddep_enter();
     extern __shared__ float S[];   // [d][kSamples]
     __shared__ float var[kMaxDim];
     __shared__ int sdim;
@@ -338,6 +374,7 @@ __device__ __forceinline__ int hist_bin(const float* coarse, const float* fine, 
 
 __global__ void k_hist(BuildArgs a, int L)
 {
+    griddep_enter();
     __shared__ float fine[32 * 33];
     __shared__ float coarse[32];
     __shared__ int hist[kSamples + 1];
@@ -415,6 +452,7 @@ static_assert(4 * kSelectThreads == kSamples, "k_select covers the sample bins w
 
 __global__ void __launch_bounds__(kSelectThreads) k_select(BuildArgs a, int L)
 {
+    griddep_enter();
     __shared__ int s_sel, s_left;
     __shared__ float shf[32];
     __shared__ int shi[33];
@@ -551,6 +589,7 @@ __global__ void __launch_bounds__(kSelectThreads) k_select(BuildArgs a, int L)
 // so a level of large nodes keeps many column loads in flight per SM.
 __global__ void k_tilecount(BuildArgs a, int L)
 {
+    griddep_enter();
     __shared__ int sh[33];
     const int cur = L & 1;
     const int ntl = a.cnt[kCntTiles0 + cur];
@@ -587,6 +626,7 @@ __global__ void k_tilecount(BuildArgs a, int L)
 // left counts within the node), one warp per node over the whole grid.
 __global__ void k_tileoff(BuildArgs a, int L)
 {
+    griddep_enter();
     const int cur = L & 1;
     const int A = a.cnt[kCntActive0 + cur];
     const int lane = threadIdx.x & 31;
@@ -609,6 +649,7 @@ __global__ void k_tileoff(BuildArgs a, int L)
 // this level, tile plan of the next level.
 __global__ void k_children(BuildArgs a, int L)
 {
+    griddep_enter();
     __shared__ int sh[33];
     __shared__ int s_next, s_small;
     const int cur = L & 1, nxt = cur ^ 1;
@@ -707,6 +748,7 @@ __global__ void k_children(BuildArgs a, int L)
 // per-tile left counts across blocks.
 __global__ void k_partition(BuildArgs a, int L)
 {
+    griddep_enter();
     __shared__ int sh[33];
     const int cur = L & 1, nxt = cur ^ 1;
     const int t = blockIdx.x;
@@ -848,6 +890,7 @@ constexpr int kSubtreeMaxWarps = 32;   // warps of the one k_subtree block per S
 
 __global__ void k_subtree(BuildArgs a, int wbytes)
 {
+    griddep_enter();
     extern __shared__ __align__(16) unsigned char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int T = a.T, d = a.d, TS = a.T + 4;
@@ -1142,6 +1185,7 @@ __global__ void k_subtree(BuildArgs a, int wbytes)
 // (the block barrier orders them), a grid covers one level.
 __global__ void k_boxes(BuildArgs a, int L_hi, int L_lo)
 {
+    griddep_enter();
     for (int L = L_hi; L >= L_lo; L--) {
         const int A = a.lvl_count[L];
         for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < A; i += gridDim.x * blockDim.x) {
@@ -1323,10 +1367,8 @@ panda_status enqueue_start(BuildState& S, cudaStream_t stream, PhaseTimer& timer
     const int sms = num_sms();
     timer.begin("transpose");
     int blocks = (int)std::min<long long>((a.n_pad + 255) / 256, (long long)sms * 16);
-    k_transpose<<<blocks, 256, 0, stream>>>(a);
-    PANDA_LAUNCHED("k_transpose");
-    k_init<<<1, 1024, 0, stream>>>(a);
-    PANDA_LAUNCHED("k_init");
+    PANDA_LAUNCH(k_transpose, blocks, 256, 0, stream, a);
+    PANDA_LAUNCH(k_init, 1, 1024, 0, stream, a);
     return PANDA_OK;
 }
 
@@ -1340,23 +1382,16 @@ panda_status enqueue_level(BuildState& S, int L, cudaStream_t stream, PhaseTimer
                                                      : (1LL << 30), pl.act_cap);
     const int tcap = (int)std::min<long long>(pl.tile_cap, (long long)a.n / kTile + 2LL * acap + 2);
     timer.begin("level.sample");
-    k_sample<<<acap, kSampleThreads, d * kSamples * 4, stream>>>(a, L);
-    PANDA_LAUNCHED("k_sample");
+    PANDA_LAUNCH(k_sample, acap, kSampleThreads, d * kSamples * 4, stream, a, L);
     timer.begin("level.hist");
-    k_hist<<<tcap, 256, 0, stream>>>(a, L);
-    PANDA_LAUNCHED("k_hist");
+    PANDA_LAUNCH(k_hist, tcap, 256, 0, stream, a, L);
     timer.begin("level.select");
-    k_select<<<acap, kSelectThreads, 0, stream>>>(a, L);
-    PANDA_LAUNCHED("k_select");
-    k_tilecount<<<std::min(tcap, 8 * num_sms()), 256, 0, stream>>>(a, L);
-    PANDA_LAUNCHED("k_tilecount");
-    k_tileoff<<<(acap + 7) / 8, 256, 0, stream>>>(a, L);
-    PANDA_LAUNCHED("k_tileoff");
-    k_children<<<1, 1024, 0, stream>>>(a, L);
-    PANDA_LAUNCHED("k_children");
+    PANDA_LAUNCH(k_select, acap, kSelectThreads, 0, stream, a, L);
+    PANDA_LAUNCH(k_tilecount, std::min(tcap, 8 * num_sms()), 256, 0, stream, a, L);
+    PANDA_LAUNCH(k_tileoff, (acap + 7) / 8, 256, 0, stream, a, L);
+    PANDA_LAUNCH(k_children, 1, 1024, 0, stream, a, L);
     timer.begin("level.partition");
-    k_partition<<<tcap, 256, 0, stream>>>(a, L);
-    PANDA_LAUNCHED("k_partition");
+    PANDA_LAUNCH(k_partition, tcap, 256, 0, stream, a, L);
     return PANDA_OK;
 }
 
@@ -1368,8 +1403,7 @@ panda_status enqueue_finish(BuildState& S, int nlevels, cudaStream_t stream, Pha
     timer.begin("subtree");
     const int wb = (int)warp_bytes(a.d, S.pl.T);
     const int wpb = S.pl.sub_warps;
-    k_subtree<<<sms, wpb * 32, (size_t)wpb * wb, stream>>>(a, wb);
-    PANDA_LAUNCHED("k_subtree");
+    PANDA_LAUNCH(k_subtree, sms, wpb * 32, (size_t)wpb * wb, stream, a, wb);
     timer.begin("boxes");
     // bottom-up: a level with more nodes than one block covers at once gets a
     // grid of its own, the levels above it go together in one block
@@ -1378,12 +1412,10 @@ panda_status enqueue_finish(BuildState& S, int nlevels, cudaStream_t stream, Pha
         const long long bound = std::min<long long>(
             L < 30 ? (1LL << L) * std::max(1, a.set_off ? a.nsets : 1) : (1LL << 30), S.pl.act_cap);
         if (bound <= 1024) break;
-        k_boxes<<<(unsigned)((bound + 255) / 256), 256, 0, stream>>>(a, L, L);
-        PANDA_LAUNCHED("k_boxes");
+        PANDA_LAUNCH(k_boxes, (unsigned)((bound + 255) / 256), 256, 0, stream, a, L, L);
     }
     if (L >= 0) {
-        k_boxes<<<1, 1024, 0, stream>>>(a, L, 0);
-        PANDA_LAUNCHED("k_boxes");
+        PANDA_LAUNCH(k_boxes, 1, 1024, 0, stream, a, L, 0);
     }
     timer.end();
     return PANDA_OK;
@@ -1562,8 +1594,7 @@ panda_status forest_enqueue(BuildState* S, cudaStream_t stream)
     const int L = forest_levels(S);
     for (int l = 0; l < L; l++)
         if ((st = enqueue_level(*S, l, stream, timer)) != PANDA_OK) return st;
-    k_check_levels<<<1, 32, 0, stream>>>(S->a, L);
-    PANDA_LAUNCHED("k_check_levels");
+    PANDA_LAUNCH(k_check_levels, 1, 32, 0, stream, S->a, L);
     return enqueue_finish(*S, L, stream, timer);
 }
 

@@ -84,6 +84,24 @@ enum : int {
     kCntSlots = 16,
 };
 
+// Programmatic dependent launch.  A kernel launched with programmatic stream
+// serialization may start while its predecessor in the stream is finishing;
+// griddep_wait() blocks until the predecessor grid has completed and its memory
+// is visible (it returns at once for a kernel launched without the attribute),
+// and griddep_launch_dependents() lets the next grid be scheduled once every
+// block of this one is running.  Every kernel of the build and query calls both
+// before it touches memory written by an earlier launch.
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void griddep_launch_dependents()
+{
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+__device__ __forceinline__ void griddep_enter()
+{
+    griddep_wait();
+    griddep_launch_dependents();
+}
+
 __device__ __forceinline__ uint32_t float_key(float f)
 {
     uint32_t u = __float_as_uint(f);

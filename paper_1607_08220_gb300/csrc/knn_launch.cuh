@@ -66,8 +66,7 @@ panda_status launch_knn_multi(const KnnArgs& a, size_t heap_bytes, cudaStream_t 
 {
     const int per_sm = multi_blocks_per_sm<DP>()[SOLO ? 1 : 0][std::min(std::max(a.k, 1), kMaxK)];
     const long long blocks = (long long)num_sms() * per_sm;
-    k_knn<DP, kKnnManySets, SOLO><<<(unsigned)blocks, kKnnThreads, heap_bytes, s>>>(a);
-    PANDA_LAUNCHED("k_knn");
+    PANDA_LAUNCH((k_knn<DP, kKnnManySets, SOLO>), (unsigned)blocks, kKnnThreads, heap_bytes, s, a);
     return PANDA_OK;
 }
 
@@ -90,25 +89,24 @@ panda_status launch_knn_dp(const KnnArgs& a, cudaStream_t s)
     if (blocks <= 0) return PANDA_OK;
     if (a.rkey) {
         if (a.solo)
-            k_knn<DP, kKnnRadius, true><<<(unsigned)blocks, kKnnThreads, heap_bytes, s>>>(a);
+            PANDA_LAUNCH((k_knn<DP, kKnnRadius, true>), (unsigned)blocks, kKnnThreads, heap_bytes, s, a);
         else
-            k_knn<DP, kKnnRadius, false><<<(unsigned)blocks, kKnnThreads, heap_bytes, s>>>(a);
+            PANDA_LAUNCH((k_knn<DP, kKnnRadius, false>), (unsigned)blocks, kKnnThreads, heap_bytes, s, a);
     } else if (a.stats || a.visits) {
         if (a.solo)
-            k_knn<DP, kKnnStats, true><<<(unsigned)blocks, kKnnThreads, heap_bytes, s>>>(a);
+            PANDA_LAUNCH((k_knn<DP, kKnnStats, true>), (unsigned)blocks, kKnnThreads, heap_bytes, s, a);
         else
-            k_knn<DP, kKnnStats, false><<<(unsigned)blocks, kKnnThreads, heap_bytes, s>>>(a);
+            PANDA_LAUNCH((k_knn<DP, kKnnStats, false>), (unsigned)blocks, kKnnThreads, heap_bytes, s, a);
     } else if (a.reqs) {
         if (a.solo)
-            k_knn<DP, kKnnOneTreeReqs, true><<<(unsigned)blocks, kKnnThreads, heap_bytes, s>>>(a);
+            PANDA_LAUNCH((k_knn<DP, kKnnOneTreeReqs, true>), (unsigned)blocks, kKnnThreads, heap_bytes, s, a);
         else
-            k_knn<DP, kKnnOneTreeReqs, false><<<(unsigned)blocks, kKnnThreads, heap_bytes, s>>>(a);
+            PANDA_LAUNCH((k_knn<DP, kKnnOneTreeReqs, false>), (unsigned)blocks, kKnnThreads, heap_bytes, s, a);
     } else if (a.solo) {
-        k_knn<DP, kKnnOneSet, true><<<(unsigned)blocks, kKnnThreads, heap_bytes, s>>>(a);
+        PANDA_LAUNCH((k_knn<DP, kKnnOneSet, true>), (unsigned)blocks, kKnnThreads, heap_bytes, s, a);
     } else {
-        k_knn<DP, kKnnOneSet, false><<<(unsigned)blocks, kKnnThreads, heap_bytes, s>>>(a);
+        PANDA_LAUNCH((k_knn<DP, kKnnOneSet, false>), (unsigned)blocks, kKnnThreads, heap_bytes, s, a);
     }
-    PANDA_LAUNCHED("k_knn");
     return PANDA_OK;
 }
 

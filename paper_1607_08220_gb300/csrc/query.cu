@@ -40,6 +40,7 @@ __device__ __forceinline__ unsigned morton_key(const OrderArgs& a, const float* 
 
 __global__ void k_order_keys(OrderArgs a)
 {
+    griddep_enter();
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= a.m) return;
     const float* q = a.queries + i * a.d;
@@ -83,6 +84,7 @@ __global__ void k_order_keys(OrderArgs a)
 // Exclusive scan of hist[0..nb) in blocks of 4096; block sums to bsum.
 __global__ void k_scan_blocks(int* hist, int nb, int* bsum)
 {
+    griddep_enter();
     __shared__ int sh[33];
     const int base = blockIdx.x * 4096 + threadIdx.x * 4;
     int v[4], t = 0;
@@ -113,6 +115,7 @@ __global__ void k_scan_blocks(int* hist, int nb, int* bsum)
 
 __global__ void k_scan_sums(int* bsum, int nblocks)
 {
+    griddep_enter();
     __shared__ int sh[33];
     __shared__ int carry;
     if (threadIdx.x == 0) carry = 0;
@@ -140,6 +143,7 @@ __global__ void k_scan_sums(int* bsum, int nblocks)
 
 __global__ void k_order_scatter(const unsigned* keys, long long m, int* cursor, const int* bsum, int* perm)
 {
+    griddep_enter();
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= m) return;
     const unsigned key = keys[i];
@@ -153,6 +157,7 @@ __global__ void k_order_scatter(const unsigned* keys, long long m, int* cursor, 
 __global__ void k_bin_jobs(const int* cursor, const int* bsum, int nb, int2* jobs, int* njobs, long long cap,
                            unsigned* err)
 {
+    griddep_enter();
     const long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31;
     int start = 0, count = 0;
@@ -313,14 +318,14 @@ panda_status knn_query(const panda_tree* t, const float* queries, int64_t m, int
         ce = cudaMemsetAsync(hist, 0, (size_t)nb * 4, stream);
         if (ce != cudaSuccess) return cleanup(), cuda_fail(ce, "clear order histogram");
         const unsigned gb = (unsigned)((m + 255) / 256);
-        k_order_keys<<<gb, 256, 0, stream>>>(oa);
-        if ((st = note_launch("k_order_keys")) != PANDA_OK) return cleanup(), st;
-        k_scan_blocks<<<nblk, 1024, 0, stream>>>(hist, nb, bsum);
-        if ((st = note_launch("k_scan_blocks")) != PANDA_OK) return cleanup(), st;
-        k_scan_sums<<<1, 1024, 0, stream>>>(bsum, nblk);
-        if ((st = note_launch("k_scan_sums")) != PANDA_OK) return cleanup(), st;
-        k_order_scatter<<<gb, 256, 0, stream>>>(keys, m, hist, bsum, perm);
-        if ((st = note_launch("k_order_scatter")) != PANDA_OK) return cleanup(), st;
+        if ((st = launch_k("k_order_keys", k_order_keys, gb, 256, 0, stream, oa)) != PANDA_OK) return cleanup(), st;
+        if ((st = launch_k("k_scan_blocks", k_scan_blocks, nblk, 1024, 0, stream, hist, nb, bsum)) != PANDA_OK)
+            return cleanup(), st;
+        if ((st = launch_k("k_scan_sums", k_scan_sums, 1, 1024, 0, stream, bsum, nblk)) != PANDA_OK)
+            return cleanup(), st;
+        if ((st = launch_k("k_order_scatter", k_order_scatter, gb, 256, 0, stream, (const unsigned*)keys, (long long)m,
+                           hist, (const int*)bsum, perm)) != PANDA_OK)
+            return cleanup(), st;
         if (order == PANDA_ORDER_LEAF && !solo && 2 * m >= t->n) {
             jobs_cap = nb + m / 32 + 1;
             void* jp = nullptr;
@@ -329,8 +334,9 @@ panda_status knn_query(const panda_tree* t, const float* queries, int64_t m, int
             jobs = reinterpret_cast<int2*>(static_cast<char*>(jp) + 16);
             ce = cudaMemsetAsync(njobs, 0, sizeof(int), stream);
             if (ce != cudaSuccess) return cleanup(), cuda_fail(ce, "clear query jobs");
-            k_bin_jobs<<<(unsigned)((nb + 255) / 256), 256, 0, stream>>>(hist, bsum, nb, jobs, njobs, jobs_cap, err);
-            if ((st = note_launch("k_bin_jobs")) != PANDA_OK) return cleanup(), st;
+            if ((st = launch_k("k_bin_jobs", k_bin_jobs, (unsigned)((nb + 255) / 256), 256, 0, stream,
+                               (const int*)hist, (const int*)bsum, nb, jobs, njobs, jobs_cap, err)) != PANDA_OK)
+                return cleanup(), st;
         }
     }
     timer.begin("query.traverse");
@@ -386,6 +392,7 @@ __device__ __forceinline__ bool leaf_of_slot(const float4* nodes, long long i, i
 // Pass 1: jobs per 1,024-position bin, and the total (one atomic per warp).
 __global__ void k_pos_jobs_count(const float4* nodes, long long slots, int ns, int* hist, int* njobs)
 {
+    griddep_enter();
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     int start = 0, count = 0, nj = 0;
     if (i < slots && leaf_of_slot(nodes, i, ns, start, count)) {
@@ -401,6 +408,7 @@ __global__ void k_pos_jobs_count(const float4* nodes, long long slots, int ns, i
 __global__ void k_pos_jobs_place(const float4* nodes, long long slots, int ns, int* cursor, const int* bsum,
                                  int2* jobs, long long cap, unsigned* err)
 {
+    griddep_enter();
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     int start = 0, count = 0;
     if (i >= slots || !leaf_of_slot(nodes, i, ns, start, count)) return;
@@ -458,20 +466,13 @@ panda_status knn_self(const panda_tree* t, int32_t k, int32_t* ids, float* d2, c
     }
     timer.begin("query.jobs");
     const unsigned gs = (unsigned)((t->node_slots + 255) / 256);
-    k_pos_jobs_count<<<gs, 256, 0, stream>>>(t->nodes, t->node_slots, t->ns, hist, njobs);
-    st = note_launch("k_pos_jobs_count");
-    if (st == PANDA_OK) {
-        k_scan_blocks<<<nblk, 1024, 0, stream>>>(hist, nb, bsum);
-        st = note_launch("k_scan_blocks");
-    }
-    if (st == PANDA_OK) {
-        k_scan_sums<<<1, 1024, 0, stream>>>(bsum, nblk);
-        st = note_launch("k_scan_sums");
-    }
-    if (st == PANDA_OK) {
-        k_pos_jobs_place<<<gs, 256, 0, stream>>>(t->nodes, t->node_slots, t->ns, hist, bsum, jobs, cap, err);
-        st = note_launch("k_pos_jobs_place");
-    }
+    st = launch_k("k_pos_jobs_count", k_pos_jobs_count, gs, 256, 0, stream, (const float4*)t->nodes,
+                  (long long)t->node_slots, t->ns, hist, njobs);
+    if (st == PANDA_OK) st = launch_k("k_scan_blocks", k_scan_blocks, nblk, 1024, 0, stream, hist, nb, bsum);
+    if (st == PANDA_OK) st = launch_k("k_scan_sums", k_scan_sums, 1, 1024, 0, stream, bsum, nblk);
+    if (st == PANDA_OK)
+        st = launch_k("k_pos_jobs_place", k_pos_jobs_place, gs, 256, 0, stream, (const float4*)t->nodes,
+                      (long long)t->node_slots, t->ns, hist, (const int*)bsum, jobs, cap, err);
     if (st != PANDA_OK) {
         ws_free(scratch, stream);
         return st;

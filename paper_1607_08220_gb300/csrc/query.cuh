@@ -597,6 +597,7 @@ constexpr int knn_min_blocks(int dp, int mode, bool solo)
 template <int DP, int MODE, bool SOLO>
 __global__ void __launch_bounds__(kKnnThreads, knn_min_blocks(DP, MODE, SOLO)) k_knn(KnnArgs a)
 {
+    griddep_enter();
     __shared__ __align__(16) float stage_x[kKnnThreads / 32][DP][32];
     __shared__ int stage_id[kKnnThreads / 32][32];
     extern __shared__ unsigned long long heap_mem[];   // [kmax + 1][kKnnThreads]

@@ -7,6 +7,7 @@
 
 #include <string>
 #include <atomic>
+#include <utility>
 #include <mutex>
 #include <vector>
 
@@ -147,6 +148,47 @@ int forest_levels(const BuildState* S);
     do {                                                        \
         cudaError_t _e = (call);                                \
         if (_e != cudaSuccess) return panda::cuda_fail(_e, what); \
+    } while (0)
+
+namespace panda {
+// Launch with programmatic stream serialization (the kernel calls
+// griddep_enter() first): the launch latency between consecutive kernels of one
+// stream overlaps the predecessor's last blocks.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t stream,
+                       Args&&... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
+// launch_pdl, counted and checked: PANDA_OK or the launch error as a status.
+template <typename... KArgs, typename... Args>
+panda_status launch_k(const char* what, void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                      cudaStream_t stream, Args&&... args)
+{
+    const cudaError_t e = launch_pdl(kernel, grid, block, smem, stream, std::forward<Args>(args)...);
+    if (e != cudaSuccess) return cuda_fail(e, what);
+    return note_launch(what);
+}
+}  // namespace panda
+
+// Launch `kernel` with programmatic dependent launch, count it and check it;
+// return the status from the enclosing function on failure.
+#define PANDA_LAUNCH(kernel, grid, block, smem, stream, ...)                                              \
+    do {                                                                                                   \
+        panda_status _ls = panda::launch_k(#kernel, kernel, dim3(grid), dim3(block), (size_t)(smem), (stream), \
+                                           __VA_ARGS__);                                                   \
+        if (_ls != PANDA_OK) return _ls;                                                                   \
     } while (0)
 
 #define PANDA_LAUNCHED(what)                                    \

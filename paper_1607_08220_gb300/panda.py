@@ -641,8 +641,10 @@ def knn_host(tree: Tree, queries: np.ndarray, k: int, order: str = "leaf", strea
     return ids, d2
 
 
-def set_phase_timing(on: bool):
-    load().panda_set_phase_timing(1 if on else 0)
+def set_phase_timing(on, traversal_only: bool = False):
+    """Per-phase CUDA-event timing of the following calls: every phase, or
+    (traversal_only) only the traversal, leaving the other kernels unseparated."""
+    load().panda_set_phase_timing((2 if traversal_only else 1) if on else 0)
 
 
 def phase_times() -> list[tuple[str, float, int]]:
