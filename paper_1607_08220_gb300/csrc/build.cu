@@ -281,6 +281,85 @@ __global__ void k_check_levels(BuildArgs a, int L)
 
 // ------------------------------------------------------------------ A2 + A3
 
+// Histogram bin of x: #{v_j <= x} over the sorted interval points, found with
+// a two-level search (every 32nd interval point first, then the 32 within).
+__device__ __forceinline__ int hist_bin(const float* coarse, const float* fine, float x)
+{
+    int cb = count_le32(coarse, x);
+    if (cb == 0) return 0;
+    int blk = cb - 1;
+    return blk * 32 + count_le32(fine + blk * 33, x);
+}
+
+constexpr int kSelectThreads = 256;   // selection blocks: 4 histogram bins per thread
+static_assert(4 * kSelectThreads == kSamples, "the selection covers the sample bins with 4 per thread");
+
+// Split selection from a node histogram (reading R3), by a block of
+// kSelectThreads threads: thread t holds bins 4t .. 4t+3; c_j = #{x < v_j} is
+// the inclusive prefix of the histogram up to bin j (one block scan of the
+// thread sums) and j* = argmin |2 c_j - cnt| with ties to the smallest j (the
+// minimum key |.| << 11 | j).  Every thread gets j* in *sel and c_{j*} in *left.
+__device__ void block_select_split(const int* bins, int cnt, int sp, int* sel, int* left)
+{
+    __shared__ int shi[33];
+    __shared__ unsigned long long s_key[kSelectThreads / 32];
+    __shared__ int s_c[kSelectThreads / 32];
+    __shared__ int s_sel, s_left;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int h[4], tot = 0;
+#pragma unroll
+    for (int e = 0; e < 4; e++) {
+        const int j = 4 * threadIdx.x + e;
+        h[e] = j < sp ? bins[j] : 0;
+        tot += h[e];
+    }
+    int total;
+    int c = block_excl_scan(tot, shi, &total);
+    unsigned long long best = ~0ull;
+    int best_c = 0;
+#pragma unroll
+    for (int e = 0; e < 4; e++) {
+        const int j = 4 * threadIdx.x + e;
+        c += h[e];
+        long long err = 2LL * c - cnt;
+        if (err < 0) err = -err;
+        const unsigned long long key = ((unsigned long long)err << 11) | (unsigned)j;
+        if (j < sp && key < best) {
+            best = key;
+            best_c = c;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {
+        const unsigned long long ob = __shfl_xor_sync(kFull, best, o);
+        const int oc = __shfl_xor_sync(kFull, best_c, o);
+        if (ob < best) {
+            best = ob;
+            best_c = oc;
+        }
+    }
+    if (lane == 0) {
+        s_key[warp] = best;
+        s_c[warp] = best_c;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long b = s_key[0];
+        int bc = s_c[0];
+        for (int w = 1; w < (int)(blockDim.x >> 5); w++)
+            if (s_key[w] < b) {
+                b = s_key[w];
+                bc = s_c[w];
+            }
+        s_sel = (int)(b & 2047ull);
+        s_left = bc;
+    }
+    __syncthreads();
+    *sel = s_sel;
+    *left = s_left;
+    __syncthreads();
+}
+
 // One block per active node: sample, per-dimension variance, split dimension,
 // bitonic sort of the sample along it.
 constexpr int kSampleThreads = 256;   // k_sample's block (8 warps over 1024 samples)
@@ -362,16 +441,6 @@ __global__ void __launch_bounds__(kSampleThreads) k_sample(BuildArgs a, int L)
 
 // ------------------------------------------------------------------ A4
 
-// Histogram bin of x: #{v_j <= x} over the sorted interval points, found with
-// a two-level search (every 32nd interval point first, then the 32 within).
-__device__ __forceinline__ int hist_bin(const float* coarse, const float* fine, float x)
-{
-    int cb = count_le32(coarse, x);
-    if (cb == 0) return 0;
-    int blk = cb - 1;
-    return blk * 32 + count_le32(fine + blk * 33, x);
-}
-
 __global__ void k_hist(BuildArgs a, int L)
 {
     griddep_enter();
@@ -447,17 +516,11 @@ __device__ int block_reduce_sum(int v, int* sh)
     return r;
 }
 
-constexpr int kSelectThreads = 256;   // k_select's block: 4 histogram bins per thread
-static_assert(4 * kSelectThreads == kSamples, "k_select covers the sample bins with 4 per thread");
-
 __global__ void __launch_bounds__(kSelectThreads) k_select(BuildArgs a, int L)
 {
     griddep_enter();
-    __shared__ int s_sel, s_left;
     __shared__ float shf[32];
     __shared__ int shi[33];
-    __shared__ unsigned long long s_key[kSelectThreads / 32];
-    __shared__ int s_c[kSelectThreads / 32];
     const int cur = L & 1;
     const int ai = blockIdx.x;
     if (ai >= a.cnt[kCntActive0 + cur]) return;
@@ -465,66 +528,14 @@ __global__ void __launch_bounds__(kSelectThreads) k_select(BuildArgs a, int L)
     const int cnt = nd.count;
     const int sp = cnt < kSamples ? cnt : kSamples;
     int mode = a.nmode[ai];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (mode == kModeValue) {
-        // thread t holds bins 4t .. 4t+3; c_j = #{x < v_j} is the inclusive
-        // prefix of the histogram up to bin j (a block scan of the thread sums)
-        const int* nh = a.nhist + (long long)ai * (kSamples + 1);
-        int h[4], tot = 0;
-#pragma unroll
-        for (int e = 0; e < 4; e++) {
-            const int j = 4 * threadIdx.x + e;
-            h[e] = j < sp ? nh[j] : 0;
-            tot += h[e];
-        }
-        int total;
-        int c = block_excl_scan(tot, shi, &total);
-        // j* = argmin |2 c_j - n|, ties to the smallest j: the minimum key (|.| << 11 | j)
-        unsigned long long best = ~0ull;
-        int best_c = 0;
-#pragma unroll
-        for (int e = 0; e < 4; e++) {
-            const int j = 4 * threadIdx.x + e;
-            c += h[e];
-            long long err = 2LL * c - cnt;
-            if (err < 0) err = -err;
-            const unsigned long long key = ((unsigned long long)err << 11) | (unsigned)j;
-            if (j < sp && key < best) {
-                best = key;
-                best_c = c;
-            }
-        }
-#pragma unroll
-        for (int o = 16; o >= 1; o >>= 1) {
-            const unsigned long long ob = __shfl_xor_sync(kFull, best, o);
-            const int oc = __shfl_xor_sync(kFull, best_c, o);
-            if (ob < best) {
-                best = ob;
-                best_c = oc;
-            }
-        }
-        if (lane == 0) {
-            s_key[warp] = best;
-            s_c[warp] = best_c;
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            unsigned long long b = s_key[0];
-            int bc = s_c[0];
-            for (int w = 1; w < (int)(blockDim.x >> 5); w++)
-                if (s_key[w] < b) {
-                    b = s_key[w];
-                    bc = s_c[w];
-                }
-            s_sel = (int)(b & 2047ull);
-            s_left = bc;
-        }
-        __syncthreads();
-        if (s_left > 0) {
+        int sel, left;
+        block_select_split(a.nhist + (long long)ai * (kSamples + 1), cnt, sp, &sel, &left);
+        if (left > 0) {
             if (threadIdx.x == 0) {
-                a.nsplit[ai] = a.vs[(long long)ai * kSamples + s_sel];
-                a.nleft[ai] = s_left;
-                a.nsel[ai] = s_sel;
+                a.nsplit[ai] = a.vs[(long long)ai * kSamples + sel];
+                a.nleft[ai] = left;
+                a.nsel[ai] = sel;
             }
             return;
         }

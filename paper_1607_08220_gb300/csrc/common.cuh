@@ -42,6 +42,9 @@ enum : int { kModeValue = 0, kModeIndex = 1, kModePending = 2 };
 // Node record: int32 a, int32 b, float split, uint32 meta, lo[DP], hi[DP], pad.
 constexpr unsigned kMetaLeaf = 0x80000000u;
 constexpr unsigned kMetaIndex = 0x40000000u;
+// Set by a refit on an inner node whose children no longer lie on their sides of
+// the split plane (a point crossed it): the plane is then no bound for pruning.
+constexpr unsigned kMetaCross = 0x20000000u;
 constexpr unsigned kMetaDimMask = 31u;
 
 // Padded dimension class used by the packed layouts and the query kernels:

@@ -530,9 +530,10 @@ __device__ __forceinline__ void knn_warp_job(const KnnArgs& a, const KnnSet& S, 
                 break;
             }
             // a lane on the near side needs the far child only if the split
-            // plane lies within its k-th distance (the far box lies beyond it)
+            // plane lies within its k-th distance (the far box lies beyond it;
+            // not for index splits, nor where a refit moved points across it)
             const float pg = __fsub_rn(qd, sv);
-            const bool far_need = need && ((meta & kMetaIndex) || right_side != right_near ||
+            const bool far_need = need && ((meta & (kMetaIndex | kMetaCross)) || right_side != right_near ||
                                            !(__fmul_rn(pg, pg) > kd));
             if (__any_sync(kFull, far_need)) stack.push(sp, h0 + (right_near ? 0 : 1), lane);
             node = h0 + (right_near ? 1 : 0);                   // near child next

@@ -97,6 +97,16 @@ __global__ void k_refit_boxes(float4* nodes, long long slots, int ns, const floa
             pr[4 + k] = fminf(__ldcg(r0 + 4 + k), __ldcg(r1 + 4 + k));
             pr[4 + dp + k] = fmaxf(__ldcg(r0 + 4 + dp + k), __ldcg(r1 + 4 + dp + k));
         }
+        // the split plane still separates the children (left box at or below
+        // it, right box at or above it) or it no longer bounds the far child
+        unsigned meta = reinterpret_cast<const unsigned*>(pr)[3];
+        if (!(meta & kMetaIndex)) {
+            const int dim = (int)(meta & kMetaDimMask);
+            const float sv = pr[2];
+            const bool sep = dim < d && __ldcg(r0 + 4 + dp + dim) <= sv && __ldcg(r1 + 4 + dim) >= sv;
+            meta = sep ? (meta & ~kMetaCross) : (meta | kMetaCross);
+            reinterpret_cast<unsigned*>(pr)[3] = meta;
+        }
         node = p;
     }
     atomicOr(err, kErrInternal);   // deeper than any valid tree
