@@ -303,6 +303,23 @@ panda_status panda_server_request_info(panda_server* server, int64_t request_id,
 int64_t panda_server_now_ns(panda_server* server);
 panda_status panda_server_stats(panda_server* server, int64_t* batches, int64_t* requests, int64_t* pending,
                                 int64_t* bytes_used);
+/* Query batches are admitted by memory as well: before a batch starts, the
+ * scheduler reserves an upper bound of its device scratch (query keys and
+ * permutation, the counting-sort histogram, request descriptors, the job
+ * queue), and the batch starts only if the reservation fits both what
+ * mem_budget_bytes leaves after the resident trees and the batches in flight,
+ * and the device's free memory (plus what the stream-ordered pool holds
+ * unused).  Requests that do not fit wait in the queue, in arrival order,
+ * until batches in flight finish; a request that cannot fit even with nothing
+ * in flight finishes with PANDA_ERR_OUT_OF_MEMORY.
+ * panda_server_set_queue_limit caps the queries waiting to be batched (0: no
+ * cap, the default): a submit that would exceed it returns
+ * PANDA_ERR_QUEUE_FULL and queues nothing.  panda_server_admission reports
+ * the scratch bytes reserved by the batches in flight, how many requests
+ * have waited for memory so far, and the queries waiting now. */
+panda_status panda_server_set_queue_limit(panda_server* server, int64_t max_pending_queries);
+panda_status panda_server_admission(panda_server* server, int64_t* scratch_reserved, int64_t* deferred_requests,
+                                    int64_t* pending_queries);
 /* Finishes queued and running requests, then releases every tree and the server. */
 void panda_server_destroy(panda_server* server);
 

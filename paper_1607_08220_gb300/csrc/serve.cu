@@ -15,6 +15,7 @@
 // and completion times.
 #include <string.h>
 
+#include <algorithm>
 #include <atomic>
 #include <chrono>
 #include <condition_variable>
@@ -87,6 +88,7 @@ struct Request {
     int64_t batch = -1;
     panda_status status = PANDA_OK;
     bool done = false;
+    bool waited = false;   // deferred at least once because its batch's scratch did not fit
 };
 
 struct InFlight {
@@ -95,7 +97,22 @@ struct InFlight {
     int slot = 0;                // pinned error region of this batch
     cudaEvent_t done = nullptr;
     std::vector<void*> scratch;
+    int64_t reserved = 0;        // scratch bytes reserved for this batch
 };
+
+// Upper bound of the device scratch enqueue_batch allocates for a batch of m
+// queries in nr requests over ng trees: keys and permutation (8 B a query),
+// the counting-sort histogram (at most 4 bins a query + 64 per tree, rounded
+// to whole 4,096-bin blocks) and its block sums, per-request descriptors and
+// error words, and the job queue of the multi-tree launch; each allocation
+// rounded up to the pool's 512-byte granularity.
+int64_t batch_scratch_bound(int64_t m, int64_t nr, int64_t ng)
+{
+    const int64_t bins = std::min<int64_t>(4 * m + 64 * ng, (int64_t)ng << 20) + 4096;
+    const int64_t bytes = 8 * m + 4 * bins + 4 * (bins / 4096 + 1) + nr * (int64_t)(sizeof(OrderSet) + sizeof(KnnReq) + 8) +
+                          ng * (int64_t)sizeof(KnnSet) + 8 * (m / 32 + ng + 1) + 64;
+    return bytes + 16 * 512;
+}
 
 }  // namespace
 
@@ -123,6 +140,14 @@ struct Server {
     std::vector<InFlight> inflight;
     int64_t next_id = 1, next_batch = 0;
     int64_t batches = 0, batched_requests = 0;
+    // Query batches are admitted by memory: each in-flight batch reserves an
+    // upper bound of its device scratch; a batch starts only if that bound fits
+    // both the budget left by the resident trees and the device's free memory
+    // (memory the stream-ordered pool holds for reuse included).
+    int64_t scratch_reserved = 0;
+    int64_t deferred = 0;            // requests that waited for memory at least once
+    int64_t pending_queries = 0;     // queries of requests not yet in a batch
+    int64_t max_pending_queries = 0; // submit refuses beyond this (0: no limit)
     bool stop = false;
     std::thread sched;
     Clock::time_point t0;
@@ -349,6 +374,8 @@ void release(Server* S, InFlight& fl)
 {
     for (void* p : fl.scratch) ws_free(p, S->qstream[fl.slot]);
     fl.scratch.clear();
+    S->scratch_reserved -= fl.reserved;
+    fl.reserved = 0;
     if (fl.done) cudaEventDestroy(fl.done);
     fl.done = nullptr;
     S->slot_busy[fl.slot] = false;
@@ -361,6 +388,29 @@ panda_status request_status(const Server* S, const InFlight& fl, size_t r)
     if (h[0] != 0) return PANDA_ERR_CUDA;
     if (h[1 + r] & kErrNonfinite) return PANDA_ERR_NONFINITE_INPUT;
     return h[1 + r] ? PANDA_ERR_CUDA : PANDA_OK;
+}
+
+// Bytes a new batch may reserve: the budget left by the resident trees and the
+// batches in flight (no budget: unbounded), and the device's free memory plus
+// what the stream-ordered pool holds unused, less what the batches in flight
+// reserved and have not allocated yet (a bound: they may have allocated some).
+int64_t scratch_available(Server* S)
+{
+    int64_t avail = INT64_MAX;
+    if (S->budget > 0) avail = S->budget - S->used - S->scratch_reserved;
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) {
+        int64_t dev = (int64_t)free_b;
+        cudaMemPool_t pool;
+        uint64_t reserved = 0, used = 0;
+        if (cudaDeviceGetDefaultMemPool(&pool, S->device) == cudaSuccess &&
+            cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &reserved) == cudaSuccess &&
+            cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &used) == cudaSuccess && reserved > used)
+            dev += (int64_t)(reserved - used);
+        avail = std::min(avail, dev - S->scratch_reserved);
+    }
+    cudaGetLastError();
+    return avail;
 }
 
 void scheduler(Server* S)
@@ -390,22 +440,60 @@ void scheduler(Server* S)
         }
         if (finished) S->cv.notify_all();
         if (S->stop && S->pending.empty() && S->inflight.empty()) break;
-        if (!S->pending.empty() && (int)S->inflight.size() < S->max_inflight) {
-            // next batch: requests in arrival order, same padded width, up to the query cap
-            std::vector<Request*> batch;
-            std::vector<int64_t> ids;
+        bool start = !S->pending.empty() && (int)S->inflight.size() < S->max_inflight;
+        std::vector<Request*> batch;
+        std::vector<int64_t> ids;
+        int64_t reserve = 0;
+        if (start) {
+            // next batch: requests in arrival order, same padded width, up to the
+            // query cap, while the batch's scratch fits the memory available
+            const int64_t avail = scratch_available(S);
             int64_t qsum = 0;
+            std::vector<int> trees_in;
             const int dp = S->trees[S->reqs[S->pending.front()].tree]->dp;
-            while (!S->pending.empty()) {
-                Request& R = S->reqs[S->pending.front()];
+            for (int64_t rid : S->pending) {
+                Request& R = S->reqs[rid];
                 if (S->trees[R.tree]->dp != dp) break;
                 if (!batch.empty() && qsum + R.m > S->max_batch_queries) break;
+                const bool new_tree = std::find(trees_in.begin(), trees_in.end(), R.tree) == trees_in.end();
+                const int64_t need = batch_scratch_bound(qsum + R.m, (int64_t)batch.size() + 1,
+                                                         (int64_t)trees_in.size() + (new_tree ? 1 : 0));
+                if (need > avail) {
+                    if (!R.waited) {
+                        R.waited = true;
+                        S->deferred++;
+                    }
+                    break;
+                }
                 batch.push_back(&R);
                 ids.push_back(R.id);
                 qsum += R.m;
-                S->pending.pop_front();
+                reserve = need;
+                if (new_tree) trees_in.push_back(R.tree);
             }
+            if (batch.empty()) {
+                start = false;
+                if (S->inflight.empty()) {
+                    // nothing runs, so nothing will free memory: the first request
+                    // can never fit; it fails instead of waiting forever
+                    Request& R = S->reqs[S->pending.front()];
+                    S->pending.pop_front();
+                    S->pending_queries -= R.m;
+                    R.status = PANDA_ERR_OUT_OF_MEMORY;
+                    R.t_done = S->now_ns();
+                    R.done = true;
+                    S->cv.notify_all();
+                    continue;
+                }
+            } else {
+                for (size_t i = 0; i < batch.size(); i++) S->pending.pop_front();
+                S->pending_queries -= qsum;
+            }
+        }
+        if (start) {
             InFlight fl;
+            fl.reserved = reserve;
+            S->scratch_reserved += reserve;
             fl.batch_id = S->next_batch++;
             fl.reqs = ids;
             while (S->slot_busy[fl.slot]) fl.slot++;   // a slot is free: fewer than kSlots in flight
@@ -555,6 +643,11 @@ panda_status panda_server_submit(panda_server* S, int32_t tree_id, const float* 
         set_error("panda_server_submit: server is shutting down");
         return PANDA_ERR_QUEUE_FULL;
     }
+    if (S->max_pending_queries > 0 && S->pending_queries + m > S->max_pending_queries) {
+        set_error("panda_server_submit: %lld queries waiting, %lld more exceed the queue limit of %lld",
+                  (long long)S->pending_queries, (long long)m, (long long)S->max_pending_queries);
+        return PANDA_ERR_QUEUE_FULL;
+    }
     Request R;
     R.id = S->next_id++;
     R.tree = tree_id;
@@ -569,7 +662,10 @@ panda_status panda_server_submit(panda_server* S, int32_t tree_id, const float* 
         R.t_done = R.t_submit;
     }
     S->reqs[R.id] = R;
-    if (m > 0) S->pending.push_back(R.id);
+    if (m > 0) {
+        S->pending.push_back(R.id);
+        S->pending_queries += m;
+    }
     *request_id = R.id;
     S->cv.notify_all();
     return PANDA_OK;
@@ -637,6 +733,28 @@ panda_status panda_server_stats(panda_server* S, int64_t* batches, int64_t* requ
     if (requests) *requests = S->batched_requests;
     if (pending) *pending = (int64_t)S->pending.size();
     if (bytes_used) *bytes_used = S->used;
+    return PANDA_OK;
+}
+
+panda_status panda_server_set_queue_limit(panda_server* S, int64_t max_pending_queries)
+{
+    if (!S || max_pending_queries < 0) {
+        set_error("panda_server_set_queue_limit: invalid argument");
+        return PANDA_ERR_INVALID_ARGUMENT;
+    }
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->max_pending_queries = max_pending_queries;
+    return PANDA_OK;
+}
+
+panda_status panda_server_admission(panda_server* S, int64_t* scratch_reserved, int64_t* deferred_requests,
+                                    int64_t* pending_queries)
+{
+    if (!S) return PANDA_ERR_INVALID_ARGUMENT;
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (scratch_reserved) *scratch_reserved = S->scratch_reserved;
+    if (deferred_requests) *deferred_requests = S->deferred;
+    if (pending_queries) *pending_queries = S->pending_queries;
     return PANDA_OK;
 }
 

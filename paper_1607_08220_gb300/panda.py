@@ -55,6 +55,8 @@ SIGNATURES = {
     "panda_server_add_tree": ([_P, _P, _I64, _I32, _I32, _P], ctypes.c_int),
     "panda_server_submit": ([_P, _I32, _P, _I64, _I32, _P, _P, _P], ctypes.c_int),
     "panda_server_poll": ([_P, _I64, _P], ctypes.c_int),
+    "panda_server_set_queue_limit": ([_P, _I64], ctypes.c_int),
+    "panda_server_admission": ([_P, _P, _P, _P], ctypes.c_int),
     "panda_server_wait": ([_P, _I64, _I64], ctypes.c_int),
     "panda_server_request_info": ([_P, _I64, _P, _P, _P], ctypes.c_int),
     "panda_server_now_ns": ([_P], _I64),
@@ -406,6 +408,18 @@ class Server:
         v = [ctypes.c_int64() for _ in range(4)]
         _check(load().panda_server_stats(self._h, *[ctypes.byref(x) for x in v]))
         return dict(zip(["batches", "requests", "pending", "bytes_used"], [x.value for x in v]))
+
+    def set_queue_limit(self, max_pending_queries: int):
+        """Cap the queries waiting to be batched (0: no cap); submit beyond it
+        raises PANDA_ERR_QUEUE_FULL."""
+        _check(load().panda_server_set_queue_limit(self._h, int(max_pending_queries)))
+
+    def admission(self) -> dict:
+        """Scratch bytes reserved by the batches in flight, requests that waited
+        for memory so far, queries waiting now."""
+        v = [ctypes.c_int64() for _ in range(3)]
+        _check(load().panda_server_admission(self._h, *[ctypes.byref(x) for x in v]))
+        return dict(zip(["scratch_reserved", "deferred_requests", "pending_queries"], [x.value for x in v]))
 
     def close(self):
         if getattr(self, "_h", None):

@@ -181,3 +181,53 @@ def test_nonfinite_request_fails_alone(P):
         ri, rd = alone(P, ref, q, 4)
         assert torch.equal(out[0], ri) and torch.equal(out[1].view(torch.int32), rd.view(torch.int32))
     srv.close()
+
+
+def test_query_batches_wait_for_memory(P):
+    """Admission of query batches by memory: with a budget that holds the tree
+    and the scratch of one 50,000-query batch but not of two (about 1.2 MB
+    against 2.5 MB), eight such requests submitted at once run one batch at a
+    time -- the others wait in the queue -- and each equals the oracle's
+    answer.  A request whose scratch can never fit fails with
+    PANDA_ERR_OUT_OF_MEMORY instead of waiting forever; a submit beyond the
+    queue limit is refused with PANDA_ERR_QUEUE_FULL."""
+    import torch
+    np_pts = workloads.cosmology_points(200_000, seed=81, halos=30)
+    ot = oracle.build(np_pts, 32)
+    pts = torch.from_numpy(np_pts).cuda()
+    probe = P.Server()
+    probe.add_tree(pts)
+    tree_bytes = probe.stats()["bytes_used"]
+    probe.close()
+    srv = P.Server(mem_budget_bytes=tree_bytes + 1_800_000)
+    t = srv.add_tree(pts)
+    reqs = []
+    for i in range(8):
+        qn = workloads.cosmology_points(50_000, seed=1100 + i, halos=30)
+        out = (torch.empty((50_000, 6), dtype=torch.int32, device="cuda"),
+               torch.empty((50_000, 6), dtype=torch.float32, device="cuda"))
+        reqs.append((qn, torch.from_numpy(qn).cuda(), out))
+    torch.cuda.synchronize()
+    rids = [srv.submit(t, qd, 6, out) for _, qd, out in reqs]
+    for rid, (qn, _, out) in zip(rids, reqs):
+        srv.wait(rid, 120)
+        assert_oracle(ot, qn, out)
+    adm = srv.admission()
+    assert adm["deferred_requests"] >= 1 and adm["scratch_reserved"] == 0 and adm["pending_queries"] == 0
+    assert srv.stats()["batches"] == 8                       # no two requests' scratch fit together
+    big = torch.from_numpy(workloads.cosmology_points(200_000, seed=1200, halos=30)).cuda()
+    out = (torch.empty((200_000, 6), dtype=torch.int32, device="cuda"),
+           torch.empty((200_000, 6), dtype=torch.float32, device="cuda"))
+    rid = srv.submit(t, big, 6, out)
+    with pytest.raises(P.PandaError) as e:
+        srv.wait(rid, 120)
+    assert e.value.status == 4
+    srv.set_queue_limit(60_000)
+    with pytest.raises(P.PandaError) as e:
+        srv.submit(t, big[:70_000], 6, (out[0][:70_000], out[1][:70_000]))
+    assert e.value.status == 7
+    qn, qd, out = reqs[0]
+    rid = srv.submit(t, qd, 6, out)                          # within the limit: accepted and exact
+    srv.wait(rid, 120)
+    assert_oracle(ot, qn, out)
+    srv.close()
