@@ -59,6 +59,10 @@ struct BuildArgs {
     int small_cap;
     int* lvl_nodes;
     int* lvl_count;
+    int* chunk_act;     // [chunks] children of level-list chunk c going to the next level
+    int* chunk_small;   // [chunks] ... going to the subtree stage
+    int* chunk_tiles;   // [chunks] tiles of next-level-list chunk c
+    int chunk_cap;
     int lvl_stride;
     int* cnt;
     unsigned* err;
@@ -125,26 +129,30 @@ __device__ int block_excl_scan(int v, int* sh /*[33]*/, int* total)
 // Tiles of the active list `x` (count A): node a covers [start, start+count),
 // cut at absolute multiples of kTile so that interior tiles are aligned.
 constexpr int kPlanPer = 4;   // consecutive active nodes per thread in one pass of the child plan
+constexpr int kChildThreads = 1024;
+constexpr int kChildChunk = kChildThreads * kPlanPer;   // level-list nodes per child-plan block
 
-__device__ void block_plan_tiles(BuildArgs& a, int x, int A)
+// Tile records of level-list nodes [lo, hi) of list x, the first at tile
+// offset `base`; returns the offset after the last.  Nodes cut into more than
+// kOwnTiles tiles (the top levels: a few nodes of many tiles each) have their
+// records written by the whole block; the thread that owns a node writes the
+// others.
+__device__ int block_plan_tiles_range(BuildArgs& a, int x, int lo, int hi, int base0)
 {
-    // Nodes cut into more than kOwnTiles tiles (the top levels: a few nodes of
-    // many tiles each) have their tile records written by the whole block; the
-    // thread that owns a node writes the others.
     constexpr int kOwnTiles = 8, kBigCap = 1024;
     __shared__ int sh[33];
     __shared__ int base, nbig;
     __shared__ int big_node[kBigCap], big_off[kBigCap], big_cnt[kBigCap];
-    if (threadIdx.x == 0) base = 0;
+    if (threadIdx.x == 0) base = base0;
     __syncthreads();
-    for (int c = 0; c < A; c += blockDim.x * kPlanPer) {
+    for (int c = lo; c < hi; c += blockDim.x * kPlanPer) {
         if (threadIdx.x == 0) nbig = 0;
         const int a0 = c + threadIdx.x * kPlanPer;
         int nt[kPlanPer], sum = 0;
 #pragma unroll
         for (int r = 0; r < kPlanPer; r++) {
             nt[r] = 0;
-            if (a0 + r < A) {
+            if (a0 + r < hi) {
                 const Active nd = a.act[x][a0 + r];
                 nt[r] = (nd.start + nd.count - 1) / kTile - nd.start / kTile + 1;
             }
@@ -155,7 +163,7 @@ __device__ void block_plan_tiles(BuildArgs& a, int x, int A)
 #pragma unroll
         for (int r = 0; r < kPlanPer; r++) {
             const int ai = a0 + r;
-            if (ai >= A) break;
+            if (ai >= hi) break;
             a.tile_base[x][ai] = off;
             int j0 = 0;
             if (nt[r] > kOwnTiles) {
@@ -200,9 +208,18 @@ __device__ void block_plan_tiles(BuildArgs& a, int x, int A)
         if (threadIdx.x == 0) base += tot;
         __syncthreads();
     }
+    const int end = base;
+    __syncthreads();
+    return end;
+}
+
+// The whole tile plan of list x (one block): tile records, bases, counts.
+__device__ void block_plan_tiles(BuildArgs& a, int x, int A)
+{
+    const int end = block_plan_tiles_range(a, x, 0, A, 0);
     if (threadIdx.x == 0) {
-        a.tile_base[x][A] = base;
-        a.cnt[kCntTiles0 + x] = min(base, a.tile_cap);
+        a.tile_base[x][A] = end;
+        a.cnt[kCntTiles0 + x] = min(end, a.tile_cap);
     }
 }
 
@@ -212,6 +229,10 @@ __device__ void block_plan_tiles(BuildArgs& a, int x, int A)
 __global__ void k_init(BuildArgs a)
 {
     griddep_enter();
+    for (int c = threadIdx.x; c < a.chunk_cap; c += blockDim.x) {
+        a.chunk_act[c] = 0;
+        a.chunk_small[c] = 0;
+    }
     __shared__ int sh[33];
     __shared__ int s_act, s_small;
     const int nsets = a.set_off ? a.nsets : 1;
@@ -360,128 +381,6 @@ __device__ void block_select_split(const int* bins, int cnt, int sp, int* sel, i
     __syncthreads();
 }
 
-// One block per active node: sample, per-dimension variance, split dimension,
-// bitonic sort of the sample along it.
-constexpr int kSampleThreads = 256;   // k_sample's block (8 warps over 1024 samples)
-
-__global__ void __launch_bounds__(kSampleThreads) k_sample(BuildArgs a, int L)
-{
-    griddep_enter();
-    extern __shared__ float S[];   // [d][kSamples]
-    __shared__ float var[kMaxDim];
-    __shared__ int sdim;
-    const int cur = L & 1;
-    const int ai = blockIdx.x;
-    if (ai >= a.cnt[kCntActive0 + cur]) return;
-    const Active nd = a.act[cur][ai];
-    const int cnt = nd.count;
-    const int sp = cnt < kSamples ? cnt : kSamples;
-    const float* X = a.X[cur];
-    for (int j = threadIdx.x; j < kSamples; j += blockDim.x) {
-        long long pos = nd.start + (long long)j * cnt / sp;
-        for (int k = 0; k < a.d; k++)
-            S[k * kSamples + j] = (j < sp) ? X[(long long)k * a.n_pad + pos] : INFINITY;
-    }
-    int* nh = a.nhist + (long long)ai * (kSamples + 1);
-    for (int b = threadIdx.x; b <= kSamples; b += blockDim.x) nh[b] = 0;
-    __syncthreads();
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    for (int k = warp; k < a.d; k += nw) {
-        const float* col = S + k * kSamples;
-        float part = 0.0f;
-        for (int j = lane; j < sp; j += 32) part = __fadd_rn(part, col[j]);
-        float mean = __fdiv_rn(fixed_order_warp_total(part), (float)sp);
-        float p2 = 0.0f;
-        for (int j = lane; j < sp; j += 32) {
-            float c = __fsub_rn(col[j], mean);
-            p2 = __fadd_rn(p2, __fmul_rn(c, c));
-        }
-        float v = __fdiv_rn(fixed_order_warp_total(p2), (float)sp);
-        if (lane == 0) var[k] = v;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int dm = argmax_dims(var, a.d, 0u);
-        sdim = dm;
-        a.ndim[ai] = dm;
-        a.nmode[ai] = (var[dm] > 0.0f) ? kModeValue : kModePending;
-        for (int k = 0; k < a.d; k++) a.nvar[ai * kMaxDim + k] = var[k];
-    }
-    __syncthreads();
-    const int dm = sdim;
-    if (!(var[dm] > 0.0f)) return;
-    // Bitonic sort.  Warp w takes the compare-exchange pairs kPairsPerWarp * w
-    // onwards, which touch only its own 2 * kPairsPerWarp elements while the
-    // stride is at most kPairsPerWarp: between two such stages a warp barrier
-    // is enough, around the wider ones the block waits.
-    constexpr int kPairsPerWarp = kSamples / 2 / (kSampleThreads / 32);
-    float* v = S + dm * kSamples;
-    for (int size = 2; size <= kSamples; size <<= 1) {
-        for (int stride = size >> 1; stride > 0; stride >>= 1) {
-#pragma unroll
-            for (int r = 0; r < kPairsPerWarp / 32; r++) {
-                const int t = warp * kPairsPerWarp + 32 * r + lane;
-                int i = 2 * t - (t & (stride - 1));
-                int j = i + stride;
-                bool up = (i & size) == 0;
-                float x = v[i], y = v[j];
-                if ((x > y) == up) {
-                    v[i] = y;
-                    v[j] = x;
-                }
-            }
-            const int next = stride > 1 ? stride >> 1 : (size < kSamples ? size : 2 * kSamples);
-            if (stride <= kPairsPerWarp && next <= kPairsPerWarp) __syncwarp();
-            else __syncthreads();
-        }
-    }
-    float* out = a.vs + (long long)ai * kSamples;
-    for (int j = threadIdx.x; j < kSamples; j += blockDim.x) out[j] = v[j];
-}
-
-// ------------------------------------------------------------------ A4
-
-__global__ void k_hist(BuildArgs a, int L)
-{
-    griddep_enter();
-    __shared__ float fine[32 * 33];
-    __shared__ float coarse[32];
-    __shared__ int hist[kSamples + 1];
-    const int cur = L & 1;
-    const int t = blockIdx.x;
-    if (t >= a.cnt[kCntTiles0 + cur]) return;
-    const Tile tl = a.tiles[cur][t];
-    const int ai = tl.node;
-    if (a.nmode[ai] != kModeValue) return;
-    const int dm = a.ndim[ai];
-    const float* vs = a.vs + (long long)ai * kSamples;
-    for (int j = threadIdx.x; j < kSamples; j += blockDim.x) {
-        float v = vs[j];
-        fine[(j >> 5) * 33 + (j & 31)] = v;
-        if ((j & 31) == 0) coarse[j >> 5] = v;
-    }
-    for (int b = threadIdx.x; b <= kSamples; b += blockDim.x) hist[b] = 0;
-    __syncthreads();
-    const float* col = a.X[cur] + (long long)dm * a.n_pad;
-    for (int i4 = (tl.begin & ~3) + 4 * threadIdx.x; i4 < tl.end; i4 += 4 * blockDim.x) {
-        float4 x4 = *reinterpret_cast<const float4*>(col + i4);
-        float xs[4] = {x4.x, x4.y, x4.z, x4.w};
-#pragma unroll
-        for (int e = 0; e < 4; e++) {
-            int i = i4 + e;
-            if (i >= tl.begin && i < tl.end) atomicAdd(&hist[hist_bin(coarse, fine, xs[e])], 1);
-        }
-    }
-    __syncthreads();
-    int* nh = a.nhist + (long long)ai * (kSamples + 1);
-    for (int b = threadIdx.x; b <= kSamples; b += blockDim.x) {
-        int h = hist[b];
-        if (h) atomicAdd(&nh[b], h);
-    }
-}
-
-// ------------------------------------------------------------------ A5 (split select)
-
 __device__ float block_reduce_min(float v, float* sh)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -516,18 +415,252 @@ __device__ int block_reduce_sum(int v, int* sh)
     return r;
 }
 
-__global__ void __launch_bounds__(kSelectThreads) k_select(BuildArgs a, int L)
+// Split of a node whose points are all samples (n_node <= 1024, so S' = n_node
+// and the sorted interval points are the node's own values): reading R3 then
+// reduces to an exact selection.  c(v) = #{x < v} grows with v, so the value
+// minimising |2 c(v) - n| (ties to the smallest) is the value vp of rank
+// floor(n/2) or the next larger value up -- no other value can do as well.  A
+// block radix selection over order-preserving keys (of x + 0: -0 and +0 are
+// one value) finds vp, skipping the key bits every value shares; one pass
+// counts na = #{x < vp}, nb = #{x <= vp} and finds up.  Every thread gets the
+// split value in *s_out and #{x < s} in *c_out (0: no value split).
+__device__ void block_exact_split(const float* vals, int cnt, float* s_out, int* c_out)
+{
+    __shared__ int rh[256];
+    __shared__ int sh[33];
+    __shared__ unsigned s_min, s_max;
+    __shared__ int s_digit, s_below;
+    __shared__ float shf[32];
+    if (threadIdx.x == 0) {
+        s_min = 0xffffffffu;
+        s_max = 0u;
+    }
+    __syncthreads();
+    unsigned kmn = 0xffffffffu, kmx = 0u;
+    for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
+        const unsigned key = float_key(__fadd_rn(vals[j], 0.0f));
+        kmn = min(kmn, key);
+        kmx = max(kmx, key);
+    }
+    atomicMin(&s_min, kmn);
+    atomicMax(&s_max, kmx);
+    __syncthreads();
+    const unsigned kmin = s_min, kmax = s_max;
+    const int top = 32 - __clz(kmin ^ kmax);
+    int rank = cnt >> 1;
+    unsigned mask = (top >= 32) ? 0u : ~((1u << top) - 1u);
+    unsigned prefix = kmin & mask;
+    for (int hi = top; hi > 0; hi -= 8) {
+        const int shift = hi >= 8 ? hi - 8 : 0;
+        const int width = hi - shift;
+        const unsigned dmask = (1u << width) - 1u;
+        for (int b = threadIdx.x; b < 256; b += blockDim.x) rh[b] = 0;
+        __syncthreads();
+        for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
+            const unsigned key = float_key(__fadd_rn(vals[j], 0.0f));
+            if ((key & mask) == prefix) atomicAdd(&rh[(key >> shift) & dmask], 1);
+        }
+        __syncthreads();
+        const int h = threadIdx.x < 256 ? rh[threadIdx.x] : 0;
+        int tot;
+        const int excl = block_excl_scan(h, sh, &tot);
+        if (threadIdx.x < 256 && h > 0 && rank >= excl && rank < excl + h) {
+            s_digit = threadIdx.x;
+            s_below = excl;
+        }
+        __syncthreads();
+        prefix |= (unsigned)s_digit << shift;
+        mask |= dmask << shift;
+        rank -= s_below;
+        __syncthreads();
+    }
+    const float vp = key_float(prefix);
+    int na = 0, nb = 0;
+    float up = INFINITY;
+    for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
+        const float x = vals[j];
+        na += x < vp;
+        nb += x <= vp;
+        if (x > vp) up = fminf(up, x);
+    }
+    na = block_reduce_sum(na, sh);
+    nb = block_reduce_sum(nb, sh);
+    up = block_reduce_min(up, shf);
+    long long e1 = 2LL * na - cnt;
+    if (e1 < 0) e1 = -e1;
+    float sv = vp;
+    int cv = na;
+    if (nb < cnt) {
+        long long e2 = 2LL * nb - cnt;
+        if (e2 < 0) e2 = -e2;
+        if (e2 < e1) {
+            sv = up;
+            cv = nb;
+        }
+    }
+    *s_out = sv;
+    *c_out = cv;
+}
+
+// One block per active node: sample, per-dimension variance, split dimension,
+// bitonic sort of the sample along it.
+constexpr int kSampleThreads = 256;   // k_sample's block (8 warps over 1024 samples)
+
+__global__ void __launch_bounds__(kSampleThreads) k_sample(BuildArgs a, int L)
 {
     griddep_enter();
-    __shared__ float shf[32];
-    __shared__ int shi[33];
+    extern __shared__ float S[];   // [d][kSamples]
+    __shared__ float var[kMaxDim];
+    __shared__ int sdim;
     const int cur = L & 1;
     const int ai = blockIdx.x;
     if (ai >= a.cnt[kCntActive0 + cur]) return;
     const Active nd = a.act[cur][ai];
     const int cnt = nd.count;
     const int sp = cnt < kSamples ? cnt : kSamples;
+    const float* X = a.X[cur];
+    for (int j = threadIdx.x; j < kSamples; j += blockDim.x) {
+        long long pos = nd.start + (long long)j * cnt / sp;
+        for (int k = 0; k < a.d; k++)
+            S[k * kSamples + j] = (j < sp) ? X[(long long)k * a.n_pad + pos] : INFINITY;
+    }
+    if (cnt > kSamples) {   // nodes of at most kSamples points are selected exactly below
+        int* nh = a.nhist + (long long)ai * (kSamples + 1);
+        for (int b = threadIdx.x; b <= kSamples; b += blockDim.x) nh[b] = 0;
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int k = warp; k < a.d; k += nw) {
+        const float* col = S + k * kSamples;
+        float part = 0.0f;
+        for (int j = lane; j < sp; j += 32) part = __fadd_rn(part, col[j]);
+        float mean = __fdiv_rn(fixed_order_warp_total(part), (float)sp);
+        float p2 = 0.0f;
+        for (int j = lane; j < sp; j += 32) {
+            float c = __fsub_rn(col[j], mean);
+            p2 = __fadd_rn(p2, __fmul_rn(c, c));
+        }
+        float v = __fdiv_rn(fixed_order_warp_total(p2), (float)sp);
+        if (lane == 0) var[k] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int dm = argmax_dims(var, a.d, 0u);
+        sdim = dm;
+        a.ndim[ai] = dm;
+        a.nmode[ai] = (var[dm] > 0.0f) ? kModeValue : kModePending;
+        for (int k = 0; k < a.d; k++) a.nvar[ai * kMaxDim + k] = var[k];
+    }
+    __syncthreads();
+    const int dm = sdim;
+    if (!(var[dm] > 0.0f)) return;
+    if (cnt <= kSamples) {
+        // every point is a sample: the exact selection (no sort, no histogram pass)
+        float sv;
+        int cv;
+        block_exact_split(S + dm * kSamples, cnt, &sv, &cv);
+        if (threadIdx.x == 0) {
+            if (cv > 0) {
+                a.nsplit[ai] = sv;
+                a.nleft[ai] = cv;
+                a.nsel[ai] = -1;
+                a.nmode[ai] = kModeSelected;
+            } else {
+                a.nmode[ai] = kModePending;   // heavy duplicates: k_select takes the fallback
+            }
+        }
+        return;
+    }
+    // Bitonic sort.  Warp w takes the compare-exchange pairs kPairsPerWarp * w
+    // onwards, which touch only its own 2 * kPairsPerWarp elements while the
+    // stride is at most kPairsPerWarp: between two such stages a warp barrier
+    // is enough, around the wider ones the block waits.
+    constexpr int kPairsPerWarp = kSamples / 2 / (kSampleThreads / 32);
+    float* v = S + dm * kSamples;
+    for (int size = 2; size <= kSamples; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+#pragma unroll
+            for (int r = 0; r < kPairsPerWarp / 32; r++) {
+                const int t = warp * kPairsPerWarp + 32 * r + lane;
+                int i = 2 * t - (t & (stride - 1));
+                int j = i + stride;
+                bool up = (i & size) == 0;
+                float x = v[i], y = v[j];
+                if ((x > y) == up) {
+                    v[i] = y;
+                    v[j] = x;
+                }
+            }
+            const int next = stride > 1 ? stride >> 1 : (size < kSamples ? size : 2 * kSamples);
+            if (stride <= kPairsPerWarp && next <= kPairsPerWarp) __syncwarp();
+            else __syncthreads();
+        }
+    }
+    float* out = a.vs + (long long)ai * kSamples;
+    for (int j = threadIdx.x; j < kSamples; j += blockDim.x) out[j] = v[j];
+}
+
+// ------------------------------------------------------------------ A4
+
+// Histogram of every tile of a value-split node over its interval points
+// (blocks stride over the tiles: levels whose nodes were selected exactly in
+// k_sample have nothing to do here).
+__global__ void k_hist(BuildArgs a, int L)
+{
+    griddep_enter();
+    __shared__ float fine[32 * 33];
+    __shared__ float coarse[32];
+    __shared__ int hist[kSamples + 1];
+    const int cur = L & 1;
+    const int ntiles = a.cnt[kCntTiles0 + cur];
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const Tile tl = a.tiles[cur][t];
+        const int ai = tl.node;
+        if (a.nmode[ai] != kModeValue) continue;
+        const int dm = a.ndim[ai];
+        const float* vs = a.vs + (long long)ai * kSamples;
+        for (int j = threadIdx.x; j < kSamples; j += blockDim.x) {
+            float v = vs[j];
+            fine[(j >> 5) * 33 + (j & 31)] = v;
+            if ((j & 31) == 0) coarse[j >> 5] = v;
+        }
+        for (int b = threadIdx.x; b <= kSamples; b += blockDim.x) hist[b] = 0;
+        __syncthreads();
+        const float* col = a.X[cur] + (long long)dm * a.n_pad;
+        for (int i4 = (tl.begin & ~3) + 4 * threadIdx.x; i4 < tl.end; i4 += 4 * blockDim.x) {
+            float4 x4 = *reinterpret_cast<const float4*>(col + i4);
+            float xs[4] = {x4.x, x4.y, x4.z, x4.w};
+#pragma unroll
+            for (int e = 0; e < 4; e++) {
+                int i = i4 + e;
+                if (i >= tl.begin && i < tl.end) atomicAdd(&hist[hist_bin(coarse, fine, xs[e])], 1);
+            }
+        }
+        __syncthreads();
+        int* nh = a.nhist + (long long)ai * (kSamples + 1);
+        for (int b = threadIdx.x; b <= kSamples; b += blockDim.x) {
+            int h = hist[b];
+            if (h) atomicAdd(&nh[b], h);
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------ A5 (split select)
+
+
+__device__ void select_node(BuildArgs& a, int cur, int ai)
+{
+    __shared__ float shf[32];
+    __shared__ int shi[33];
+    const Active nd = a.act[cur][ai];
+    const int cnt = nd.count;
+    const int sp = cnt < kSamples ? cnt : kSamples;
     int mode = a.nmode[ai];
+    // k_sample selected the split exactly.  The mode stays kModeSelected (the
+    // later kernels tell only index splits apart): a write here would race with
+    // the block's other warps still reading it.
+    if (mode == kModeSelected) return;
     if (mode == kModeValue) {
         int sel, left;
         block_select_split(a.nhist + (long long)ai * (kSamples + 1), cnt, sp, &sel, &left);
@@ -595,6 +728,18 @@ __global__ void __launch_bounds__(kSelectThreads) k_select(BuildArgs a, int L)
     }
 }
 
+// Split selection of every node of the level (blocks stride over the nodes).
+__global__ void __launch_bounds__(kSelectThreads) k_select(BuildArgs a, int L)
+{
+    griddep_enter();
+    const int cur = L & 1;
+    const int A = a.cnt[kCntActive0 + cur];
+    for (int ai = blockIdx.x; ai < A; ai += gridDim.x) {
+        select_node(a, cur, ai);
+        __syncthreads();
+    }
+}
+
 // Per-tile count of left points for nodes that span several tiles.
 // Left count of every tile: one block per tile (grid-stride over the tiles),
 // so a level of large nodes keeps many column loads in flight per SM.
@@ -638,119 +783,182 @@ __global__ void k_tilecount(BuildArgs a, int L)
 __global__ void k_tileoff(BuildArgs a, int L)
 {
     griddep_enter();
+    __shared__ int s_act, s_small;
     const int cur = L & 1;
     const int A = a.cnt[kCntActive0 + cur];
     const int lane = threadIdx.x & 31;
-    const int ai = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (ai >= A) return;
-    const int tb = min(a.tile_base[cur][ai], a.tile_cap);
-    const int te = min(a.tile_base[cur][ai + 1], a.tile_cap);
-    int running = 0;
-    for (int j0 = tb; j0 < te; j0 += 32) {
-        int j = j0 + lane;
-        int v = j < te ? a.tleft[j] : 0;
-        int incl = warp_incl_scan(v);
-        if (j < te) a.tleftoff[j] = running + incl - v;
-        running += __shfl_sync(kFull, incl, 31);
+    // the next level's tile sums (k_children adds, k_plan reads) start at zero
+    if (blockIdx.x == 0)
+        for (int c = threadIdx.x; c < a.chunk_cap; c += blockDim.x) a.chunk_tiles[c] = 0;
+    if (threadIdx.x == 0) {
+        s_act = 0;
+        s_small = 0;
     }
-    if (lane == 0 && running != a.nleft[ai]) atomicOr(a.err, kErrInternal);
+    __syncthreads();
+    const int ai = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (ai < A) {
+        if (lane == 0) {
+            // children of node ai: to the next level (more than T points) or the subtree stage
+            const int cl = a.nleft[ai], cr = a.act[cur][ai].count - cl;
+            const int act = (cl > a.T) + (cr > a.T);
+            atomicAdd(&s_act, act);
+            atomicAdd(&s_small, 2 - act);
+        }
+        const int tb = min(a.tile_base[cur][ai], a.tile_cap);
+        const int te = min(a.tile_base[cur][ai + 1], a.tile_cap);
+        int running = 0;
+        for (int j0 = tb; j0 < te; j0 += 32) {
+            int j = j0 + lane;
+            int v = j < te ? a.tleft[j] : 0;
+            int incl = warp_incl_scan(v);
+            if (j < te) a.tleftoff[j] = running + incl - v;
+            running += __shfl_sync(kFull, incl, 31);
+        }
+        if (lane == 0 && running != a.nleft[ai]) atomicOr(a.err, kErrInternal);
+    }
+    __syncthreads();
+    // this block's nodes lie in one chunk (blockDim / 32 divides kChildChunk)
+    const int first = blockIdx.x * (blockDim.x >> 5);
+    if (threadIdx.x == 0 && first < A) {
+        const int c = first / kChildChunk;
+        if (s_act) atomicAdd(&a.chunk_act[c], s_act);
+        if (s_small) atomicAdd(&a.chunk_small[c], s_small);
+    }
 }
 
-// One block: children creation (next level or subtree stage), node headers of
-// this level, tile plan of the next level.
+// Children of the level's nodes (next level or subtree stage), node headers of
+// this level: one block per chunk of kChildChunk level-list nodes.  A block's
+// first list positions are the sums of the chunks before it (from k_tileoff),
+// so the lists come out in node order without any block waiting for another.
+// Each block also adds the tile counts of the next-level nodes it creates to
+// the chunk sums k_plan needs.  Counters are updated by k_plan.
 __global__ void k_children(BuildArgs a, int L)
 {
     griddep_enter();
     __shared__ int sh[33];
-    __shared__ int s_next, s_small;
+    __shared__ int s_tiles[3];
     const int cur = L & 1, nxt = cur ^ 1;
     const int A = a.cnt[kCntActive0 + cur];
+    const int c = blockIdx.x;
+    const int lo = c * kChildChunk;
+    if (lo >= A) return;
+    const int hi = min(A, lo + kChildChunk);
     const int base_id = a.cnt[kCntNodes];
-    if (threadIdx.x == 0) {
-        s_next = 0;
-        s_small = a.cnt[kCntSmall];
+    int act_base = 0, small_base = a.cnt[kCntSmall];
+    for (int p = 0; p < c; p++) {
+        act_base += a.chunk_act[p];
+        small_base += a.chunk_small[p];
     }
-    __syncthreads();
-    for (int c0 = 0; c0 < A; c0 += blockDim.x * kPlanPer) {
-        // thread t plans nodes a0 .. a0 + kPlanPer - 1: one block scan of its
-        // (children to the next level << 16 | children to the subtree stage);
-        // a pass holds at most 2 kPlanPer blockDim children of either kind < 2^16
-        const int a0 = c0 + threadIdx.x * kPlanPer;
-        int nxt_cnt = 0, sm_cnt = 0;
+    const int first_chunk = act_base / kChildChunk;
+    if (threadIdx.x < 3) s_tiles[threadIdx.x] = 0;
+    // thread t plans nodes a0 .. a0 + kPlanPer - 1 of the chunk: one block scan
+    // of (children to the next level << 16 | children to the subtree stage)
+    static_assert(2 * kChildChunk < (1 << 16), "packed child counts");
+    const int a0 = lo + threadIdx.x * kPlanPer;
+    int nxt_cnt = 0, sm_cnt = 0;
 #pragma unroll
-        for (int r = 0; r < kPlanPer; r++) {
-            if (a0 + r < A) {
-                const int cl = a.nleft[a0 + r], cr = a.act[cur][a0 + r].count - cl;
-                const int act = (cl > a.T) + (cr > a.T);
-                nxt_cnt += act;
-                sm_cnt += 2 - act;
-            }
+    for (int r = 0; r < kPlanPer; r++) {
+        if (a0 + r < hi) {
+            const int cl = a.nleft[a0 + r], cr = a.act[cur][a0 + r].count - cl;
+            const int act = (cl > a.T) + (cr > a.T);
+            nxt_cnt += act;
+            sm_cnt += 2 - act;
         }
-        int tot;
-        const int pk = block_excl_scan((nxt_cnt << 16) | sm_cnt, sh, &tot);
-        int ia = s_next + (pk >> 16), is = s_small + (pk & 0xffff);
-        for (int r = 0; r < kPlanPer; r++) {
-            const int ai = a0 + r;
-            if (ai >= A) break;
-            const Active nd = a.act[cur][ai];
-            const int cl = a.nleft[ai], cr = nd.count - cl;
-            const int child = base_id + 2 * ai;
-            const int cdepth = nd.depth + 1;
-            for (int side = 0; side < 2; side++) {
-                const int cs = side ? nd.start + cl : nd.start;
-                const int cc = side ? cr : cl;
-                if (cc > a.T) {
-                    if (cdepth >= kMaxDepth) atomicOr(a.err, kErrDepth);
-                    if (ia < a.act_cap) {
-                        Active c;
-                        c.start = cs;
-                        c.count = cc;
-                        c.node = child + side;
-                        c.depth = cdepth;
-                        a.act[nxt][ia] = c;
-                    } else {
-                        atomicOr(a.err, kErrActiveOverflow);
-                    }
-                    ia++;
-                } else {
-                    if (is < a.small_cap) {
-                        Small sm;
-                        sm.start = cs;
-                        sm.count = cc;
-                        sm.node = child + side;
-                        sm.depth_parity = (cdepth << 1) | nxt;
-                        a.small[is] = sm;
-                    } else {
-                        atomicOr(a.err, kErrSmallOverflow);
-                    }
-                    is++;
-                }
-            }
-            const int mode = a.nmode[ai];
-            if (nd.node < a.node_cap) {
-                unsigned meta = (unsigned)a.ndim[ai] | (mode == kModeIndex ? kMetaIndex : 0u);
-                int4 h = make_int4(child, 0, __float_as_int(a.nsplit[ai]), (int)meta);
-                reinterpret_cast<int4*>(a.nodes)[(long long)nd.node * a.ns] = h;
-            }
-            a.lvl_nodes[L * a.lvl_stride + ai] = nd.node;
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            s_next += tot >> 16;
-            s_small += tot & 0xffff;
-        }
-        __syncthreads();
     }
-    if (threadIdx.x == 0) {
-        a.cnt[kCntNodes] = base_id + 2 * A;
-        if (base_id + 2 * A > a.node_cap) atomicOr(a.err, kErrNodeOverflow);
-        a.cnt[kCntActive0 + nxt] = min(s_next, a.act_cap);
-        a.cnt[kCntSmall] = s_small;
-        a.lvl_count[L] = A;
-        if (A > 0) a.cnt[kCntLevels] = L + 1;
+    int tot;
+    const int pk = block_excl_scan((nxt_cnt << 16) | sm_cnt, sh, &tot);
+    int ia = act_base + (pk >> 16), is = small_base + (pk & 0xffff);
+    for (int r = 0; r < kPlanPer; r++) {
+        const int ai = a0 + r;
+        if (ai >= hi) break;
+        const Active nd = a.act[cur][ai];
+        const int cl = a.nleft[ai], cr = nd.count - cl;
+        const int child = base_id + 2 * ai;
+        const int cdepth = nd.depth + 1;
+        for (int side = 0; side < 2; side++) {
+            const int cs = side ? nd.start + cl : nd.start;
+            const int cc = side ? cr : cl;
+            if (cc > a.T) {
+                if (cdepth >= kMaxDepth) atomicOr(a.err, kErrDepth);
+                if (ia < a.act_cap) {
+                    Active ch;
+                    ch.start = cs;
+                    ch.count = cc;
+                    ch.node = child + side;
+                    ch.depth = cdepth;
+                    a.act[nxt][ia] = ch;
+                    const int nt = (cs + cc - 1) / kTile - cs / kTile + 1;
+                    const int slot = ia / kChildChunk - first_chunk;   // 0..2: a block's children span <= 3 chunks
+                    if (slot >= 0 && slot < 3) atomicAdd(&s_tiles[slot], nt);
+                    else atomicOr(a.err, kErrInternal);
+                } else {
+                    atomicOr(a.err, kErrActiveOverflow);
+                }
+                ia++;
+            } else {
+                if (is < a.small_cap) {
+                    Small sm;
+                    sm.start = cs;
+                    sm.count = cc;
+                    sm.node = child + side;
+                    sm.depth_parity = (cdepth << 1) | nxt;
+                    a.small[is] = sm;
+                } else {
+                    atomicOr(a.err, kErrSmallOverflow);
+                }
+                is++;
+            }
+        }
+        const int mode = a.nmode[ai];
+        if (nd.node < a.node_cap) {
+            unsigned meta = (unsigned)a.ndim[ai] | (mode == kModeIndex ? kMetaIndex : 0u);
+            int4 h = make_int4(child, 0, __float_as_int(a.nsplit[ai]), (int)meta);
+            reinterpret_cast<int4*>(a.nodes)[(long long)nd.node * a.ns] = h;
+        }
+        a.lvl_nodes[L * a.lvl_stride + ai] = nd.node;
     }
     __syncthreads();
-    block_plan_tiles(a, nxt, min(s_next, a.act_cap));
+    if (threadIdx.x < 3 && s_tiles[threadIdx.x] > 0 && first_chunk + (int)threadIdx.x < a.chunk_cap)
+        atomicAdd(&a.chunk_tiles[first_chunk + threadIdx.x], s_tiles[threadIdx.x]);
+}
+
+// Tile plan of the next level, one block per chunk of kChildChunk next-level
+// nodes (tile offsets from the chunk sums of k_children); block 0 also updates
+// the level counters and the last tile base.  (The child sums are read by
+// every block here; k_partition clears them for the next level.)
+__global__ void k_plan(BuildArgs a, int L)
+{
+    griddep_enter();
+    const int cur = L & 1, nxt = cur ^ 1;
+    const int A = a.cnt[kCntActive0 + cur];
+    int an = 0, as = 0, at = 0;
+    const int nchunks = min((A + kChildChunk - 1) / kChildChunk, a.chunk_cap);
+    for (int p = 0; p < nchunks; p++) {
+        an += a.chunk_act[p];
+        as += a.chunk_small[p];
+    }
+    const int An = min(an, a.act_cap);
+    const int c = blockIdx.x;
+    const int lo = c * kChildChunk;
+    int tile_base0 = 0;
+    const int nxt_chunks = min((An + kChildChunk - 1) / kChildChunk, a.chunk_cap);
+    for (int p = 0; p < c && p < nxt_chunks; p++) tile_base0 += a.chunk_tiles[p];
+    for (int p = 0; p < nxt_chunks; p++) at += a.chunk_tiles[p];
+    if (lo < An) block_plan_tiles_range(a, nxt, lo, min(An, lo + kChildChunk), tile_base0);
+    if (c == 0) {
+        if (threadIdx.x == 0) {
+            a.tile_base[nxt][An] = at;
+            a.cnt[kCntTiles0 + nxt] = min(at, a.tile_cap);
+            const int base_id = a.cnt[kCntNodes];
+            a.cnt[kCntNodes] = base_id + 2 * A;
+            if (base_id + 2 * A > a.node_cap) atomicOr(a.err, kErrNodeOverflow);
+            a.cnt[kCntActive0 + nxt] = An;
+            if (an > a.act_cap) atomicOr(a.err, kErrActiveOverflow);
+            a.cnt[kCntSmall] += as;
+            a.lvl_count[L] = A;
+            if (A > 0) a.cnt[kCntLevels] = L + 1;
+        }
+    }
 }
 
 // Stable partition of every tile: left (x[dim] < s, or the first half for an
@@ -763,6 +971,11 @@ __global__ void k_partition(BuildArgs a, int L)
     __shared__ int sh[33];
     const int cur = L & 1, nxt = cur ^ 1;
     const int t = blockIdx.x;
+    if (t == 0)   // the next level's child sums (k_tileoff adds, k_children and k_plan read)
+        for (int c = threadIdx.x; c < a.chunk_cap; c += blockDim.x) {
+            a.chunk_act[c] = 0;
+            a.chunk_small[c] = 0;
+        }
     if (t >= a.cnt[kCntTiles0 + cur]) return;
     const Tile tl = a.tiles[cur][t];
     const int ai = tl.node;
@@ -1242,10 +1455,16 @@ struct Buffers {
     }
 };
 
+// Nodes of at most T points go to the subtree stage (one warp each, in shared
+// memory); above it the level passes split them.  512 rather than 1024: the
+// subtree stage then runs about twice the warps per SM (2^24 cosmology build:
+// subtree 2.61 -> 1.57 ms), and the extra level pass costs less than that,
+// since nodes of at most 1024 points are split by exact selection in k_sample
+// (all their points are samples) and the child plan is one block per chunk.
 int subtree_threshold(int d, int bucket)
 {
     (void)d;
-    int T = 1024;
+    int T = 512;
     return std::max(T, bucket);
 }
 
@@ -1334,6 +1553,10 @@ panda_status build_alloc(BuildState& S, int n, int d, cudaStream_t stream)
     GET(a.small, (size_t)pl.small_cap, "subtree list");
     GET(a.lvl_nodes, (size_t)pl.lvl_stride * pl.max_levels, "level nodes");
     GET(a.lvl_count, (size_t)pl.max_levels, "level counts");
+    a.chunk_cap = pl.act_cap / kChildChunk + 2;
+    GET(a.chunk_act, (size_t)a.chunk_cap, "child sums");
+    GET(a.chunk_small, (size_t)a.chunk_cap, "child sums");
+    GET(a.chunk_tiles, (size_t)a.chunk_cap, "tile sums");
     GET(a.cnt, (size_t)kCntSlots, "counters");
     GET(a.err, (size_t)1, "error word");
 #undef GET
@@ -1395,12 +1618,15 @@ panda_status enqueue_level(BuildState& S, int L, cudaStream_t stream, PhaseTimer
     timer.begin("level.sample");
     PANDA_LAUNCH(k_sample, acap, kSampleThreads, d * kSamples * 4, stream, a, L);
     timer.begin("level.hist");
-    PANDA_LAUNCH(k_hist, tcap, 256, 0, stream, a, L);
+    PANDA_LAUNCH(k_hist, std::min(tcap, 8 * num_sms()), 256, 0, stream, a, L);
     timer.begin("level.select");
-    PANDA_LAUNCH(k_select, acap, kSelectThreads, 0, stream, a, L);
+    PANDA_LAUNCH(k_select, std::min(acap, 8 * num_sms()), kSelectThreads, 0, stream, a, L);
     PANDA_LAUNCH(k_tilecount, std::min(tcap, 8 * num_sms()), 256, 0, stream, a, L);
     PANDA_LAUNCH(k_tileoff, (acap + 7) / 8, 256, 0, stream, a, L);
-    PANDA_LAUNCH(k_children, 1, 1024, 0, stream, a, L);
+    const int nchunk = (acap + kChildChunk - 1) / kChildChunk;
+    const int nxt_cap = (int)std::min<long long>(2LL * acap, pl.act_cap);
+    PANDA_LAUNCH(k_children, nchunk, kChildThreads, 0, stream, a, L);
+    PANDA_LAUNCH(k_plan, (nxt_cap + kChildChunk - 1) / kChildChunk, kChildThreads, 0, stream, a, L);
     timer.begin("level.partition");
     PANDA_LAUNCH(k_partition, tcap, 256, 0, stream, a, L);
     return PANDA_OK;

@@ -37,7 +37,10 @@ enum : unsigned {
 };
 
 // Split modes of a node.
-enum : int { kModeValue = 0, kModeIndex = 1, kModePending = 2 };
+// kModeSelected: a value split whose split value and left count k_sample
+// already found by exact selection (every point of the node is a sample);
+// every kernel after the selection treats it as a value split.
+enum : int { kModeValue = 0, kModeIndex = 1, kModePending = 2, kModeSelected = 3 };
 
 // Node record: int32 a, int32 b, float split, uint32 meta, lo[DP], hi[DP], pad.
 constexpr unsigned kMetaLeaf = 0x80000000u;
