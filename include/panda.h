@@ -354,8 +354,10 @@ panda_status panda_tune_lookup(int32_t d, int64_t n, int32_t k, int64_t m_total,
  * padded coordinates are 0.  Node record: int32 a, int32 b, float split,
  * uint32 meta, then lo[dp], hi[dp], zero padding to a multiple of 4 floats;
  * meta bit 31 = leaf, bit 30 = index split, bits 0..4 = split dimension; an
- * inner node's children are nodes a and a+1; a leaf holds the packed points
- * a .. a+b-1.  Packed point: dp coordinates, then the point's id as int32
+ * inner node's children are nodes a and a+1 and b is the right child's first
+ * packed position (the all-points query walks down to a leaf by it; a table
+ * with other b values still answers exactly, only slower); a leaf holds the
+ * packed points a .. a+b-1.  Packed point: dp coordinates, then the point's id as int32
  * bits in float slot dp, zero padding to a multiple of 4 floats. */
 panda_status panda_tree_get_info(const panda_tree* tree, panda_tree_info* info);
 panda_status panda_tree_copy(const panda_tree* tree, float* host_nodes, float* host_points);

@@ -912,7 +912,7 @@ __global__ void k_children(BuildArgs a, int L)
         const int mode = a.nmode[ai];
         if (nd.node < a.node_cap) {
             unsigned meta = (unsigned)a.ndim[ai] | (mode == kModeIndex ? kMetaIndex : 0u);
-            int4 h = make_int4(child, 0, __float_as_int(a.nsplit[ai]), (int)meta);
+            int4 h = make_int4(child, nd.start + cl, __float_as_int(a.nsplit[ai]), (int)meta);
             reinterpret_cast<int4*>(a.nodes)[(long long)nd.node * a.ns] = h;
         }
         a.lvl_nodes[L * a.lvl_stride + ai] = nd.node;
@@ -1381,7 +1381,7 @@ __global__ void k_subtree(BuildArgs a, int wbytes)
             const int c0 = pool_next;
             pool_next += 2;
             unsigned meta = (unsigned)dim | (mode == kModeIndex ? kMetaIndex : 0u);
-            write_node(a, node, make_int4(c0, 0, __float_as_int(s), (int)meta), w.box);
+            write_node(a, node, make_int4(c0, start + ls + cleft, __float_as_int(s), (int)meta), w.box);
             my_nodes++;
             __syncwarp();
             if (lane == 0) {

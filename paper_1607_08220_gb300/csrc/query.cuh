@@ -361,6 +361,24 @@ __device__ __forceinline__ void knn_warp_job(const KnnArgs& a, const KnnSet& S, 
     WarpStack stack;
     int sp = 0;
     int node = S.root;
+    if (!REQS && a.self_q) {
+        // All-points query: the warp's queries are points of the leaf holding
+        // position g0.  With no k-th distance known yet every lane needs every
+        // node above that leaf, so walk straight down to it (go right where g0
+        // is at or past the right child's first position), push each far
+        // child, and start the search there.  Any leaf would keep the result
+        // exact: the far children and the path cover the whole tree.
+        for (int lv = 0; lv <= kMaxDepth; lv++) {
+            if ((unsigned)node >= (unsigned)S.num_nodes || sp >= WarpStack::kCap) break;  // flagged below
+            const int4 hd = __ldg(reinterpret_cast<const int4*>(S.nodes + (long long)node * NS));
+            if ((unsigned)hd.w & kMetaLeaf) break;
+            const int right = g0 >= hd.y ? 1 : 0;
+            stack.push(sp, hd.x + 1 - right, lane);
+            node = hd.x + right;
+            if (STATS) vnodes += valid;
+            if (stats) st[0]++;
+        }
+    }
     // A valid tree is visited in at most 2 * num_nodes steps; the cap only
     // guarantees termination (with an error flag) should a node table be corrupt.
     unsigned budget = (unsigned)min(S.num_nodes + 8, 0xffffffffLL);

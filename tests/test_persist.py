@@ -77,3 +77,41 @@ def test_save_load_round_trip(tmp_path):
         x, y = fn(t), fn(u)
         torch.cuda.synchronize()
         assert torch.equal(x[0], y[0]) and torch.equal(x[1].view(torch.int32), y[1].view(torch.int32))
+
+
+@pytest.mark.gpu
+def test_inner_right_start_is_only_a_hint(tmp_path):
+    """The all-points query walks down to each job's leaf by the inner nodes'
+    second header word (the right child's first packed position).  A table
+    whose inner nodes hold other values there (zeros: always right; random
+    words) still answers exactly: the walk's far children and its path cover
+    the whole tree whichever leaf it reaches."""
+    import torch
+    P = _lib()
+    P.load()
+    pts = workloads.cosmology_points(60_000, seed=35, halos=12)
+    t = P.build(torch.from_numpy(pts).cuda(), 32)
+    want = P.knn_self(t, 7)
+    torch.cuda.synchronize()
+    path = str(tmp_path / "tree.bin")
+    P.save(t, path)
+    raw = bytearray(open(path, "rb").read())
+    hdr = struct.unpack_from("<12q", raw, len(MAGIC))
+    ns, slots = hdr[5], hdr[7]
+    off = len(MAGIC) + 12 * 8 + 32 * 4
+    nodes = np.frombuffer(bytes(raw[off:off + slots * ns * 16]), np.int32).reshape(slots, ns * 4).copy()
+    inner = (nodes[:, 3].view(np.uint32) & 0x80000000) == 0
+    assert inner.sum() > 1000
+    rng = np.random.default_rng(36)
+    for variant in ("zero", "random"):
+        nodes[inner, 1] = 0 if variant == "zero" else rng.integers(-2**31, 2**31 - 1, inner.sum())
+        raw[off:off + nodes.nbytes] = nodes.tobytes()
+        p2 = str(tmp_path / f"tree_{variant}.bin")
+        with open(p2, "wb") as f:
+            f.write(raw)
+        u = P.load_tree(p2)
+        got = P.knn_self(u, 7)
+        torch.cuda.synchronize()
+        assert torch.equal(got[0], want[0]) and torch.equal(got[1].view(torch.int32), want[1].view(torch.int32)), variant
+        u.free()
+    t.free()
