@@ -312,20 +312,46 @@ __device__ __forceinline__ int hist_bin(const float* coarse, const float* fine, 
     return blk * 32 + count_le32(fine + blk * 33, x);
 }
 
+// The first histogram pass of a node counts bins one by one only for the
+// interval points of sample ranks kWinLo .. kWinHi, around the median rank
+// 512 where c_j crosses n/2 (the sample's median rank of the node's median has
+// a standard deviation of about 16; the window spans 8 of them each way), and
+// only the count of points below v_kWinLo outside it.  For j in the window,
+// c_j = #{x < v_kWinLo} + the window bins up to j, which is all the selection
+// reads when 2 c_kWinLo <= n <= 2 c_kWinHi: every j below the window then has
+// |2 c_j - n| >= |2 c_kWinLo - n| (equal only for v_j = v_kWinLo, so the
+// same split value and count), and every j above it |2 c_j - n| >=
+// |2 c_kWinHi - n|.  Otherwise the node takes the full histogram.
+constexpr int kWinLo = 384, kWinHi = 640, kWin = kWinHi - kWinLo;
+static_assert(kWin == 256 && kWinHi < kSamples, "count_le256 covers the window");
+
+// #{a_i <= x} over 256 sorted values (binary search, branch-free).
+__device__ __forceinline__ int count_le256(const float* a, float x)
+{
+    int c = 0;
+#pragma unroll
+    for (int s = 128; s >= 1; s >>= 1)
+        if (a[c + s - 1] <= x) c += s;
+    if (a[c] <= x) c++;
+    return c;
+}
+
 constexpr int kSelectThreads = 256;   // selection blocks: 4 histogram bins per thread
 static_assert(4 * kSelectThreads == kSamples, "the selection covers the sample bins with 4 per thread");
+static_assert(kSamples == 1024, "sample positions use a shift by 10");
 
 // Split selection from a node histogram (reading R3), by a block of
 // kSelectThreads threads: thread t holds bins 4t .. 4t+3; c_j = #{x < v_j} is
 // the inclusive prefix of the histogram up to bin j (one block scan of the
 // thread sums) and j* = argmin |2 c_j - cnt| with ties to the smallest j (the
-// minimum key |.| << 11 | j).  Every thread gets j* in *sel and c_{j*} in *left.
-__device__ void block_select_split(const int* bins, int cnt, int sp, int* sel, int* left)
+// minimum key |.| << 11 | j).  Every thread gets j* in *sel and c_{j*} in *left,
+// and the prefixes c_kWinLo and c_kWinHi in *c_lo and *c_hi.
+__device__ void block_select_split(const int* bins, int cnt, int sp, int* sel, int* left, int* c_lo, int* c_hi)
 {
     __shared__ int shi[33];
     __shared__ unsigned long long s_key[kSelectThreads / 32];
     __shared__ int s_c[kSelectThreads / 32];
-    __shared__ int s_sel, s_left;
+    __shared__ int s_sel, s_left, s_clo, s_chi;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int h[4], tot = 0;
 #pragma unroll
@@ -342,6 +368,8 @@ __device__ void block_select_split(const int* bins, int cnt, int sp, int* sel, i
     for (int e = 0; e < 4; e++) {
         const int j = 4 * threadIdx.x + e;
         c += h[e];
+        if (j == kWinLo) s_clo = c;
+        if (j == kWinHi) s_chi = c;
         long long err = 2LL * c - cnt;
         if (err < 0) err = -err;
         const unsigned long long key = ((unsigned long long)err << 11) | (unsigned)j;
@@ -378,6 +406,8 @@ __device__ void block_select_split(const int* bins, int cnt, int sp, int* sel, i
     __syncthreads();
     *sel = s_sel;
     *left = s_left;
+    *c_lo = s_clo;
+    *c_hi = s_chi;
     __syncthreads();
 }
 
@@ -424,6 +454,9 @@ __device__ int block_reduce_sum(int v, int* sh)
 // one value) finds vp, skipping the key bits every value shares; one pass
 // counts na = #{x < vp}, nb = #{x <= vp} and finds up.  Every thread gets the
 // split value in *s_out and #{x < s} in *c_out (0: no value split).
+constexpr int kSampleThreads = 256;   // k_sample's block (8 warps over 1024 samples)
+constexpr int kSamplePer = kSamples / kSampleThreads;
+
 __device__ void block_exact_split(const float* vals, int cnt, float* s_out, int* c_out)
 {
     __shared__ int rh[256];
@@ -435,13 +468,23 @@ __device__ void block_exact_split(const float* vals, int cnt, float* s_out, int*
         s_min = 0xffffffffu;
         s_max = 0u;
     }
-    __syncthreads();
+    // the thread's values and their keys stay in registers for every pass
+    float xv[kSamplePer];
+    unsigned key[kSamplePer];
+    bool ok[kSamplePer];
     unsigned kmn = 0xffffffffu, kmx = 0u;
-    for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
-        const unsigned key = float_key(__fadd_rn(vals[j], 0.0f));
-        kmn = min(kmn, key);
-        kmx = max(kmx, key);
+#pragma unroll
+    for (int r = 0; r < kSamplePer; r++) {
+        const int j = threadIdx.x + r * kSampleThreads;
+        ok[r] = j < cnt;
+        xv[r] = ok[r] ? vals[j] : 0.0f;
+        key[r] = float_key(__fadd_rn(xv[r], 0.0f));
+        if (ok[r]) {
+            kmn = min(kmn, key[r]);
+            kmx = max(kmx, key[r]);
+        }
     }
+    __syncthreads();
     atomicMin(&s_min, kmn);
     atomicMax(&s_max, kmx);
     __syncthreads();
@@ -454,17 +497,16 @@ __device__ void block_exact_split(const float* vals, int cnt, float* s_out, int*
         const int shift = hi >= 8 ? hi - 8 : 0;
         const int width = hi - shift;
         const unsigned dmask = (1u << width) - 1u;
-        for (int b = threadIdx.x; b < 256; b += blockDim.x) rh[b] = 0;
+        rh[threadIdx.x] = 0;
         __syncthreads();
-        for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
-            const unsigned key = float_key(__fadd_rn(vals[j], 0.0f));
-            if ((key & mask) == prefix) atomicAdd(&rh[(key >> shift) & dmask], 1);
-        }
+#pragma unroll
+        for (int r = 0; r < kSamplePer; r++)
+            if (ok[r] && (key[r] & mask) == prefix) atomicAdd(&rh[(key[r] >> shift) & dmask], 1);
         __syncthreads();
-        const int h = threadIdx.x < 256 ? rh[threadIdx.x] : 0;
+        const int h = rh[threadIdx.x];
         int tot;
         const int excl = block_excl_scan(h, sh, &tot);
-        if (threadIdx.x < 256 && h > 0 && rank >= excl && rank < excl + h) {
+        if (h > 0 && rank >= excl && rank < excl + h) {
             s_digit = threadIdx.x;
             s_below = excl;
         }
@@ -477,8 +519,10 @@ __device__ void block_exact_split(const float* vals, int cnt, float* s_out, int*
     const float vp = key_float(prefix);
     int na = 0, nb = 0;
     float up = INFINITY;
-    for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
-        const float x = vals[j];
+#pragma unroll
+    for (int r = 0; r < kSamplePer; r++) {
+        if (!ok[r]) continue;
+        const float x = xv[r];
         na += x < vp;
         nb += x <= vp;
         if (x > vp) up = fminf(up, x);
@@ -504,7 +548,6 @@ __device__ void block_exact_split(const float* vals, int cnt, float* s_out, int*
 
 // One block per active node: sample, per-dimension variance, split dimension,
 // bitonic sort of the sample along it.
-constexpr int kSampleThreads = 256;   // k_sample's block (8 warps over 1024 samples)
 
 __global__ void __launch_bounds__(kSampleThreads) k_sample(BuildArgs a, int L)
 {
@@ -514,13 +557,15 @@ __global__ void __launch_bounds__(kSampleThreads) k_sample(BuildArgs a, int L)
     __shared__ int sdim;
     const int cur = L & 1;
     const int ai = blockIdx.x;
+    if (ai == 0 && threadIdx.x == 0) a.cnt[kCntRehist] = 0;   // the level's window misses
     if (ai >= a.cnt[kCntActive0 + cur]) return;
     const Active nd = a.act[cur][ai];
     const int cnt = nd.count;
     const int sp = cnt < kSamples ? cnt : kSamples;
     const float* X = a.X[cur];
     for (int j = threadIdx.x; j < kSamples; j += blockDim.x) {
-        long long pos = nd.start + (long long)j * cnt / sp;
+        // floor(j * cnt / sp): j itself when sp = cnt, a shift when sp = 1024
+        const long long pos = nd.start + (sp == kSamples ? ((long long)j * cnt) >> 10 : (long long)j);
         for (int k = 0; k < a.d; k++)
             S[k * kSamples + j] = (j < sp) ? X[(long long)k * a.n_pad + pos] : INFINITY;
     }
@@ -602,12 +647,86 @@ __global__ void __launch_bounds__(kSampleThreads) k_sample(BuildArgs a, int L)
 
 // ------------------------------------------------------------------ A4
 
-// Histogram of every tile of a value-split node over its interval points
-// (blocks stride over the tiles: levels whose nodes were selected exactly in
-// k_sample have nothing to do here).
+// Window histogram of every tile of a value-split node (blocks stride over
+// the tiles: levels whose nodes were selected exactly in k_sample have nothing
+// to do here).  A point below v_kWinLo adds to bin kWinLo (c_kWinLo is then
+// exact), one in [v_kWinLo, v_kWinHi) to its own bin #{v_j <= x} (a search of
+// the 256 window points), and one at or above v_kWinHi to nothing.
 __global__ void k_hist(BuildArgs a, int L)
 {
     griddep_enter();
+    __shared__ float win[kWin];
+    __shared__ int hist[kWin];
+    __shared__ int sh[33];
+    __shared__ float queue[256 / 32][64];   // a warp's window values waiting for their search
+    const int cur = L & 1;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float* qw = queue[warp];
+    const int ntiles = a.cnt[kCntTiles0 + cur];
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const Tile tl = a.tiles[cur][t];
+        const int ai = tl.node;
+        if (a.nmode[ai] != kModeValue) continue;
+        const int dm = a.ndim[ai];
+        const float* vs = a.vs + (long long)ai * kSamples;
+        for (int j = threadIdx.x; j < kWin; j += blockDim.x) {
+            win[j] = vs[kWinLo + j];
+            hist[j] = 0;
+        }
+        const float vlo = vs[kWinLo], vhi = vs[kWinHi];
+        __syncthreads();
+        const float* col = a.X[cur] + (long long)dm * a.n_pad;
+        int below = 0;
+        // Values in the window are queued per warp and searched 32 at a time,
+        // so every lane of a search has a value (about a quarter of them fall
+        // in the window).  The trip count is warp-uniform.
+        int qn = 0;
+        for (int w0 = (tl.begin & ~3) + 4 * (threadIdx.x & ~31); w0 < tl.end; w0 += 4 * blockDim.x) {
+            const int i4 = w0 + 4 * lane;
+            float4 x4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            if (i4 < tl.end) x4 = *reinterpret_cast<const float4*>(col + i4);
+            const float xs[4] = {x4.x, x4.y, x4.z, x4.w};
+#pragma unroll
+            for (int e = 0; e < 4; e++) {
+                const int i = i4 + e;
+                const bool in = i >= tl.begin && i < tl.end;
+                const float x = xs[e];
+                below += in && x < vlo;
+                const bool w = in && x >= vlo && x < vhi;
+                const unsigned m = __ballot_sync(kFull, w);
+                if (w) qw[qn + __popc(m & lanemask_lt())] = x;
+                qn += __popc(m);
+                if (qn >= 32) {
+                    __syncwarp();
+                    const float y = qw[lane];
+                    const float rest = lane + 32 < qn ? qw[lane + 32] : 0.0f;
+                    __syncwarp();
+                    if (lane + 32 < qn) qw[lane] = rest;
+                    qn -= 32;
+                    atomicAdd(&hist[count_le256(win, y) - 1], 1);
+                }
+            }
+        }
+        __syncwarp();
+        if (lane < qn) atomicAdd(&hist[count_le256(win, qw[lane]) - 1], 1);
+        below = block_reduce_sum(below, sh);
+        int* nh = a.nhist + (long long)ai * (kSamples + 1);
+        if (threadIdx.x == 0 && below) atomicAdd(&nh[kWinLo], below);
+        for (int b = threadIdx.x; b < kWin; b += blockDim.x) {
+            const int h = hist[b];
+            if (h) atomicAdd(&nh[kWinLo + 1 + b], h);
+        }
+        __syncthreads();
+    }
+}
+
+// Full histogram of every tile of a node the window missed, over all its
+// interval points (a two-level search: every 32nd interval point, then the 32
+// within); the launch returns at once when no node was missed.
+__global__ void k_hist_full(BuildArgs a, int L)
+{
+    griddep_enter();
+    if (a.cnt[kCntRehist] == 0) return;
     __shared__ float fine[32 * 33];
     __shared__ float coarse[32];
     __shared__ int hist[kSamples + 1];
@@ -616,7 +735,7 @@ __global__ void k_hist(BuildArgs a, int L)
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const Tile tl = a.tiles[cur][t];
         const int ai = tl.node;
-        if (a.nmode[ai] != kModeValue) continue;
+        if (a.nmode[ai] != kModeRehist) continue;
         const int dm = a.ndim[ai];
         const float* vs = a.vs + (long long)ai * kSamples;
         for (int j = threadIdx.x; j < kSamples; j += blockDim.x) {
@@ -649,6 +768,10 @@ __global__ void k_hist(BuildArgs a, int L)
 // ------------------------------------------------------------------ A5 (split select)
 
 
+// FULL = false: the split from the window histogram (a node whose crossing
+// lies outside the window is marked kModeRehist, its histogram cleared for the
+// full pass).  FULL = true: the split of a kModeRehist node from the full one.
+template <bool FULL>
 __device__ void select_node(BuildArgs& a, int cur, int ai)
 {
     __shared__ float shf[32];
@@ -661,14 +784,24 @@ __device__ void select_node(BuildArgs& a, int cur, int ai)
     // later kernels tell only index splits apart): a write here would race with
     // the block's other warps still reading it.
     if (mode == kModeSelected) return;
-    if (mode == kModeValue) {
-        int sel, left;
-        block_select_split(a.nhist + (long long)ai * (kSamples + 1), cnt, sp, &sel, &left);
+    if (mode == (FULL ? kModeRehist : kModeValue)) {
+        int sel, left, c_lo, c_hi;
+        int* nh = a.nhist + (long long)ai * (kSamples + 1);
+        block_select_split(nh, cnt, sp, &sel, &left, &c_lo, &c_hi);
+        if (!FULL && (2LL * c_lo > cnt || 2LL * c_hi < cnt)) {
+            for (int b = threadIdx.x; b <= kSamples; b += blockDim.x) nh[b] = 0;
+            if (threadIdx.x == 0) {
+                a.nmode[ai] = kModeRehist;
+                atomicAdd(&a.cnt[kCntRehist], 1);
+            }
+            return;
+        }
         if (left > 0) {
             if (threadIdx.x == 0) {
                 a.nsplit[ai] = a.vs[(long long)ai * kSamples + sel];
                 a.nleft[ai] = left;
                 a.nsel[ai] = sel;
+                if (FULL) a.nmode[ai] = kModeValue;
             }
             return;
         }
@@ -735,7 +868,21 @@ __global__ void __launch_bounds__(kSelectThreads) k_select(BuildArgs a, int L)
     const int cur = L & 1;
     const int A = a.cnt[kCntActive0 + cur];
     for (int ai = blockIdx.x; ai < A; ai += gridDim.x) {
-        select_node(a, cur, ai);
+        select_node<false>(a, cur, ai);
+        __syncthreads();
+    }
+}
+
+// Selection of the nodes the window missed, from their full histograms.
+__global__ void __launch_bounds__(kSelectThreads) k_select_full(BuildArgs a, int L)
+{
+    griddep_enter();
+    if (a.cnt[kCntRehist] == 0) return;
+    const int cur = L & 1;
+    const int A = a.cnt[kCntActive0 + cur];
+    for (int ai = blockIdx.x; ai < A; ai += gridDim.x) {
+        if (a.nmode[ai] != kModeRehist) continue;
+        select_node<true>(a, cur, ai);
         __syncthreads();
     }
 }
@@ -766,12 +913,23 @@ __global__ void k_tilecount(BuildArgs a, int L)
         const float s = a.nsplit[ai];
         const float* col = a.X[cur] + (long long)a.ndim[ai] * a.n_pad;
         int c = 0;
-        for (int i4 = (tl.begin & ~3) + 4 * threadIdx.x; i4 < tl.end; i4 += 4 * blockDim.x) {
-            float4 x4 = *reinterpret_cast<const float4*>(col + i4);
-            c += (i4 >= tl.begin && i4 < tl.end && x4.x < s);
-            c += (i4 + 1 >= tl.begin && i4 + 1 < tl.end && x4.y < s);
-            c += (i4 + 2 >= tl.begin && i4 + 2 < tl.end && x4.z < s);
-            c += (i4 + 3 >= tl.begin && i4 + 3 < tl.end && x4.w < s);
+        // four float4 loads in flight per thread before any is used
+        const int step = 4 * blockDim.x;
+        for (int i0 = (tl.begin & ~3) + 4 * threadIdx.x; i0 < tl.end; i0 += 4 * step) {
+            float4 x4[4];
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                const int p = i0 + u * step;
+                x4[u] = p < tl.end ? *reinterpret_cast<const float4*>(col + p) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                const int p = i0 + u * step;
+                c += (p >= tl.begin && p < tl.end && x4[u].x < s);
+                c += (p + 1 >= tl.begin && p + 1 < tl.end && x4[u].y < s);
+                c += (p + 2 >= tl.begin && p + 2 < tl.end && x4[u].z < s);
+                c += (p + 3 >= tl.begin && p + 3 < tl.end && x4[u].w < s);
+            }
         }
         const int v = block_reduce_sum(c, sh);
         if (threadIdx.x == 0) a.tleft[t] = v;
@@ -1621,6 +1779,8 @@ panda_status enqueue_level(BuildState& S, int L, cudaStream_t stream, PhaseTimer
     PANDA_LAUNCH(k_hist, std::min(tcap, 8 * num_sms()), 256, 0, stream, a, L);
     timer.begin("level.select");
     PANDA_LAUNCH(k_select, std::min(acap, 8 * num_sms()), kSelectThreads, 0, stream, a, L);
+    PANDA_LAUNCH(k_hist_full, std::min(tcap, 8 * num_sms()), 256, 0, stream, a, L);
+    PANDA_LAUNCH(k_select_full, std::min(acap, 8 * num_sms()), kSelectThreads, 0, stream, a, L);
     PANDA_LAUNCH(k_tilecount, std::min(tcap, 8 * num_sms()), 256, 0, stream, a, L);
     PANDA_LAUNCH(k_tileoff, (acap + 7) / 8, 256, 0, stream, a, L);
     const int nchunk = (acap + kChildChunk - 1) / kChildChunk;

@@ -40,7 +40,10 @@ enum : unsigned {
 // kModeSelected: a value split whose split value and left count k_sample
 // already found by exact selection (every point of the node is a sample);
 // every kernel after the selection treats it as a value split.
-enum : int { kModeValue = 0, kModeIndex = 1, kModePending = 2, kModeSelected = 3 };
+// kModeRehist: a value split whose crossing of n/2 fell outside the window of
+// interval points the first histogram counts one by one; a second pass
+// histograms it over all interval points, and it is a value split after that.
+enum : int { kModeValue = 0, kModeIndex = 1, kModePending = 2, kModeSelected = 3, kModeRehist = 4 };
 
 // Node record: int32 a, int32 b, float split, uint32 meta, lo[DP], hi[DP], pad.
 constexpr unsigned kMetaLeaf = 0x80000000u;
@@ -87,6 +90,7 @@ enum : int {
     kCntDepth = 8,
     kCntLevels = 9,    // number of level-stage levels that had active nodes
     kCntRealNodes = 10, // nodes written by the subtree stage (the rest of its id range are holes)
+    kCntRehist = 11,   // nodes of the current level marked kModeRehist
     kCntSlots = 16,
 };
 

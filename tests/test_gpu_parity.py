@@ -106,6 +106,17 @@ def _edge_cases():
         yield f"k{k}", rng.random((9000, 3), dtype=np.float32), rng.random((100, 3), dtype=np.float32), k, 32
     for B in (1, 2, 5, 64, 256):
         yield f"B{B}", rng.random((5000, 3), dtype=np.float32), rng.random((99, 3), dtype=np.float32), 6, B
+    # every strided sample of the root in the lowest (highest) quarter of the
+    # split dimension's values: c_j crosses n/2 outside the window of interval
+    # points the first histogram pass counts, and the root takes the full pass
+    m = 40
+    for name, base in (("window_miss_below", 0.0), ("window_miss_above", 0.75)):
+        x = rng.random((1024 * m, 3), dtype=np.float32) * np.float32(0.1)
+        u = rng.random(1024 * m, dtype=np.float32)
+        on_sample = np.arange(1024 * m) % m == 0
+        rest = np.float32(0.25) if base == 0.0 else np.float32(0.0)
+        x[:, 0] = np.where(on_sample, np.float32(base) + np.float32(0.25) * u, rest + np.float32(0.75) * u)
+        yield name, x, rng.random((300, 3), dtype=np.float32), 6, 32
     yield "neg_zero", np.array([[-0.0, 1.0], [0.0, 1.0], [0.0, -0.0], [-0.0, 0.0], [1.0, 1.0]] * 20,
                                np.float32), np.array([[0.0, 0.0], [-0.0, 0.5]], np.float32), 7, 4
     # hand-worked nodes whose split dimension depends on the exact FP32
