@@ -128,8 +128,8 @@ __device__ int block_excl_scan(int v, int* sh /*[33]*/, int* total)
 
 // Tiles of the active list `x` (count A): node a covers [start, start+count),
 // cut at absolute multiples of kTile so that interior tiles are aligned.
-constexpr int kPlanPer = 4;   // consecutive active nodes per thread in one pass of the child plan
-constexpr int kChildThreads = 1024;
+constexpr int kPlanPer = 1;   // consecutive active nodes per thread in one pass of the child plan
+constexpr int kChildThreads = 256;
 constexpr int kChildChunk = kChildThreads * kPlanPer;   // level-list nodes per child-plan block
 
 // Tile records of level-list nodes [lo, hi) of list x, the first at tile
