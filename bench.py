@@ -257,8 +257,8 @@ def run_reference(args):
 # `kernel_sha1`; once they change, the figure is dropped (traffic: null) until
 # the committed ncu capture is taken again.
 KNN_TRAFFIC = {"workload": "cosmology_self", "path": "self", "d": 3, "k": 10,
-               "bytes_per_query": (0.960031e9 + 1.077305e9) / 2 ** 23,
-               "kernel_sha1": "8578b3f954abd6453a137b6e58c2b4de2a125d21",
+               "bytes_per_query": (0.962653e9 + 1.086922e9) / 2 ** 23,
+               "kernel_sha1": "5e704dcc9b219d413609aa176d2ab64beb024bcb",
                "source": "one ncu capture of k_knn at n = m = 2^23 (cosmology self-KNN), scaled by queries"}
 KNN_SOURCES = ("query.cuh", "knn_launch.cuh", "common.cuh")
 
@@ -480,6 +480,24 @@ def run_ours(args):
         outs = [(a_.numpy(), b_.numpy()) for a_, b_ in keep]
         streams = [torch.cuda.Stream(), torch.cuda.Stream()]
 
+        # the host link of this machine (pinned buffer of one result array, best of
+        # two copies each way, outside the timed region): e2e is bound by it
+        def link_gbs(dst, src):
+            best = float("inf")
+            for _ in range(2):
+                c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                c0.record(stream)
+                dst.copy_(src, non_blocking=True)
+                c1.record(stream)
+                torch.cuda.synchronize()
+                best = min(best, c0.elapsed_time(c1))
+            return src.numel() * src.element_size() / (best * 1e6)
+
+        probe_dev = torch.empty_like(keep[0][0], device="cuda")
+        link = {"h2d_gbs": link_gbs(probe_dev, keep[0][0]), "d2h_gbs": link_gbs(keep[0][0], probe_dev),
+                "bytes": int(probe_dev.numel() * probe_dev.element_size())}
+        del probe_dev
+
         def step_e2e(i):
             if use_self:
                 s_ = streams[i % 2]
@@ -509,7 +527,7 @@ def run_ours(args):
         e_ms = max_over_ranks(e0.elapsed_time(e1), world, "cuda")
         e2e = {"value": whole_job_rate(m * args.steps, world, e_ms / 1e3), "unit": UNIT,
                "h2d_bytes_per_step": int(w.points.nbytes + (0 if use_self else w.queries.nbytes)),
-               "d2h_bytes_per_step": int(m * k * 8), "ms_per_step": e_ms / args.steps,
+               "d2h_bytes_per_step": int(m * k * 8), "ms_per_step": e_ms / args.steps, "host_link": link,
                "path": ("panda_build_host + panda_knn_self_host_async + panda_free_async, two steps in flight "
                         "on two streams" if use_self else "panda_build_host + panda_knn_host, one step after "
                                                           "the other")}

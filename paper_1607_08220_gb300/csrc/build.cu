@@ -133,84 +133,55 @@ constexpr int kChildThreads = 256;
 constexpr int kChildChunk = kChildThreads * kPlanPer;   // level-list nodes per child-plan block
 
 // Tile records of level-list nodes [lo, hi) of list x, the first at tile
-// offset `base`; returns the offset after the last.  Nodes cut into more than
-// kOwnTiles tiles (the top levels: a few nodes of many tiles each) have their
-// records written by the whole block; the thread that owns a node writes the
-// others.
+// offset `base0`; returns the offset after the last.  Per chunk of blockDim
+// nodes one block scan gives every node's first tile, and the block's threads
+// then take the chunk's tiles in turn, each finding its node by a binary
+// search of those offsets, so a node cut into many tiles (the top levels) and
+// many nodes of a few tiles each (the deep levels) keep every thread busy.
 __device__ int block_plan_tiles_range(BuildArgs& a, int x, int lo, int hi, int base0)
 {
-    constexpr int kOwnTiles = 8, kBigCap = 1024;
+    constexpr int kMaxThreads = 1024;
     __shared__ int sh[33];
-    __shared__ int base, nbig;
-    __shared__ int big_node[kBigCap], big_off[kBigCap], big_cnt[kBigCap];
-    if (threadIdx.x == 0) base = base0;
-    __syncthreads();
-    for (int c = lo; c < hi; c += blockDim.x * kPlanPer) {
-        if (threadIdx.x == 0) nbig = 0;
-        const int a0 = c + threadIdx.x * kPlanPer;
-        int nt[kPlanPer], sum = 0;
-#pragma unroll
-        for (int r = 0; r < kPlanPer; r++) {
-            nt[r] = 0;
-            if (a0 + r < hi) {
-                const Active nd = a.act[x][a0 + r];
-                nt[r] = (nd.start + nd.count - 1) / kTile - nd.start / kTile + 1;
-            }
-            sum += nt[r];
+    __shared__ int s_off[kMaxThreads], s_start[kMaxThreads], s_end[kMaxThreads];
+    int base = base0;
+    for (int c = lo; c < hi; c += blockDim.x) {
+        const int ai = c + threadIdx.x;
+        int nt = 0;
+        if (ai < hi) {
+            const Active nd = a.act[x][ai];
+            nt = (nd.start + nd.count - 1) / kTile - nd.start / kTile + 1;
+            s_start[threadIdx.x] = nd.start;
+            s_end[threadIdx.x] = nd.start + nd.count;
         }
         int tot;
-        int off = block_excl_scan(sum, sh, &tot) + base;   // (its barriers also order nbig = 0)
+        const int excl = block_excl_scan(nt, sh, &tot);
+        s_off[threadIdx.x] = excl;
+        if (ai < hi) a.tile_base[x][ai] = base + excl;
+        __syncthreads();
+        const int nn = min((int)blockDim.x, hi - c);
+        for (int q = threadIdx.x; q < tot; q += blockDim.x) {
+            // the chunk's node holding tile q: the last r with s_off[r] <= q
+            int r = 0;
 #pragma unroll
-        for (int r = 0; r < kPlanPer; r++) {
-            const int ai = a0 + r;
-            if (ai >= hi) break;
-            a.tile_base[x][ai] = off;
-            int j0 = 0;
-            if (nt[r] > kOwnTiles) {
-                const int slot = atomicAdd(&nbig, 1);
-                if (slot < kBigCap) {
-                    big_node[slot] = ai;
-                    big_off[slot] = off;
-                    big_cnt[slot] = nt[r];
-                    j0 = nt[r];   // written below by the block
-                }
+            for (int step = kMaxThreads / 2; step >= 1; step >>= 1)
+                if (r + step < nn && s_off[r + step] <= q) r += step;
+            if (base + q >= a.tile_cap) {
+                atomicOr(a.err, kErrTileOverflow);
+                continue;
             }
-            const Active nd = a.act[x][ai];
-            const int first = nd.start / kTile;
-            for (int j = j0; j < nt[r]; j++) {
-                if (off + j >= a.tile_cap) { atomicOr(a.err, kErrTileOverflow); break; }
-                Tile t;
-                t.node = ai;
-                t.begin = max(nd.start, (first + j) * kTile);
-                t.end = min(nd.start + nd.count, (first + j + 1) * kTile);
-                t.first = (j == 0);
-                a.tiles[x][off + j] = t;
-            }
-            off += nt[r];
+            const int j = q - s_off[r];
+            const int first = s_start[r] / kTile;
+            Tile t;
+            t.node = c + r;
+            t.begin = max(s_start[r], (first + j) * kTile);
+            t.end = min(s_end[r], (first + j + 1) * kTile);
+            t.first = (j == 0);
+            a.tiles[x][base + q] = t;
         }
-        __syncthreads();
-        const int nb = min(nbig, kBigCap);
-        for (int e = 0; e < nb; e++) {
-            const int ai = big_node[e], o = big_off[e], cnt = big_cnt[e];
-            const Active nd = a.act[x][ai];
-            const int first = nd.start / kTile;
-            for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
-                if (o + j >= a.tile_cap) { atomicOr(a.err, kErrTileOverflow); break; }
-                Tile t;
-                t.node = ai;
-                t.begin = max(nd.start, (first + j) * kTile);
-                t.end = min(nd.start + nd.count, (first + j + 1) * kTile);
-                t.first = (j == 0);
-                a.tiles[x][o + j] = t;
-            }
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) base += tot;
+        base += tot;
         __syncthreads();
     }
-    const int end = base;
-    __syncthreads();
-    return end;
+    return base;
 }
 
 // The whole tile plan of list x (one block): tile records, bases, counts.
@@ -868,6 +839,7 @@ __global__ void __launch_bounds__(kSelectThreads) k_select(BuildArgs a, int L)
     const int cur = L & 1;
     const int A = a.cnt[kCntActive0 + cur];
     for (int ai = blockIdx.x; ai < A; ai += gridDim.x) {
+        if (a.nmode[ai] == kModeSelected) continue;   // split in k_sample; no shared memory touched
         select_node<false>(a, cur, ai);
         __syncthreads();
     }
