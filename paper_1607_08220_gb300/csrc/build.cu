@@ -416,91 +416,127 @@ __device__ int block_reduce_sum(int v, int* sh)
     return r;
 }
 
-// Split of a node whose points are all samples (n_node <= 1024, so S' = n_node
-// and the sorted interval points are the node's own values): reading R3 then
-// reduces to an exact selection.  c(v) = #{x < v} grows with v, so the value
+constexpr int kSampleThreads = 256;   // k_sample's block (8 warps over 1024 samples)
+constexpr int kSmallWarps = 8;        // k_sample_small: nodes per block, one per warp
+
+// Split of a level-stage node whose points are all samples (n_node <= 1024,
+// so S' = n_node), one warp per node.  R1's sample is then the node's own
+// column runs, so R2's variances are taken over them in the order k_sample's
+// samples would have (element j into partial j mod 32), and reading R3
+// reduces to an exact selection: c(v) = #{x < v} grows with v, so the value
 // minimising |2 c(v) - n| (ties to the smallest) is the value vp of rank
 // floor(n/2) or the next larger value up -- no other value can do as well.  A
-// block radix selection over order-preserving keys (of x + 0: -0 and +0 are
-// one value) finds vp, skipping the key bits every value shares; one pass
-// counts na = #{x < vp}, nb = #{x <= vp} and finds up.  Every thread gets the
-// split value in *s_out and #{x < s} in *c_out (0: no value split).
-constexpr int kSampleThreads = 256;   // k_sample's block (8 warps over 1024 samples)
-constexpr int kSamplePer = kSamples / kSampleThreads;
-
-__device__ void block_exact_split(const float* vals, int cnt, float* s_out, int* c_out)
+// radix selection over order-preserving keys (of x + 0: -0 and +0 are one
+// value) finds vp, skipping the key bits every value shares; one pass counts
+// na = #{x < vp}, nb = #{x <= vp} and finds up.  No sort, histogram pass or
+// selection kernel runs for such a node (its mode becomes kModeSelected).
+__global__ void __launch_bounds__(kSmallWarps * 32) k_sample_small(BuildArgs a, int L)
 {
-    __shared__ int rh[256];
-    __shared__ int sh[33];
-    __shared__ unsigned s_min, s_max;
-    __shared__ int s_digit, s_below;
-    __shared__ float shf[32];
-    if (threadIdx.x == 0) {
-        s_min = 0xffffffffu;
-        s_max = 0u;
-    }
-    // the thread's values and their keys stay in registers for every pass
-    float xv[kSamplePer];
-    unsigned key[kSamplePer];
-    bool ok[kSamplePer];
-    unsigned kmn = 0xffffffffu, kmx = 0u;
-#pragma unroll
-    for (int r = 0; r < kSamplePer; r++) {
-        const int j = threadIdx.x + r * kSampleThreads;
-        ok[r] = j < cnt;
-        xv[r] = ok[r] ? vals[j] : 0.0f;
-        key[r] = float_key(__fadd_rn(xv[r], 0.0f));
-        if (ok[r]) {
-            kmn = min(kmn, key[r]);
-            kmx = max(kmx, key[r]);
+    griddep_enter();
+    __shared__ float s_vals[kSmallWarps][kSamples];
+    __shared__ int s_rh[kSmallWarps][256];
+    __shared__ float s_var[kSmallWarps][kMaxDim];
+    const int cur = L & 1;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int ai = blockIdx.x * kSmallWarps + warp;
+    if (ai >= a.cnt[kCntActive0 + cur]) return;
+    const Active nd = a.act[cur][ai];
+    const int cnt = nd.count;
+    if (cnt > kSamples) return;   // a sampled node: k_sample
+    const float* X = a.X[cur];
+    float* var = s_var[warp];
+    for (int k = 0; k < a.d; k++) {
+        const float* col = X + (long long)k * a.n_pad + nd.start;
+        float part = 0.0f;
+        for (int j = lane; j < cnt; j += 32) part = __fadd_rn(part, col[j]);
+        const float mean = __fdiv_rn(fixed_order_warp_total(part), (float)cnt);
+        float p2 = 0.0f;
+        for (int j = lane; j < cnt; j += 32) {
+            const float c = __fsub_rn(col[j], mean);
+            p2 = __fadd_rn(p2, __fmul_rn(c, c));
         }
+        const float v = __fdiv_rn(fixed_order_warp_total(p2), (float)cnt);
+        if (lane == 0) var[k] = v;
     }
-    __syncthreads();
-    atomicMin(&s_min, kmn);
-    atomicMax(&s_max, kmx);
-    __syncthreads();
-    const unsigned kmin = s_min, kmax = s_max;
-    const int top = 32 - __clz(kmin ^ kmax);
+    __syncwarp();
+    const int dm = argmax_dims(var, a.d, 0u);
+    if (lane == 0) {
+        a.ndim[ai] = dm;
+        for (int k = 0; k < a.d; k++) a.nvar[ai * kMaxDim + k] = var[k];
+    }
+    if (!(var[dm] > 0.0f)) {
+        if (lane == 0) a.nmode[ai] = kModePending;   // constant along every dim: k_select's fallback
+        return;
+    }
+    float* vals = s_vals[warp];
+    int* rh = s_rh[warp];
+    const float* col = X + (long long)dm * a.n_pad + nd.start;
+    unsigned kmn = 0xffffffffu, kmx = 0u;
+    for (int j = lane; j < cnt; j += 32) {
+        const float x = col[j];
+        vals[j] = x;
+        const unsigned key = float_key(__fadd_rn(x, 0.0f));
+        kmn = min(kmn, key);
+        kmx = max(kmx, key);
+    }
+    kmn = __reduce_min_sync(kFull, kmn);
+    kmx = __reduce_max_sync(kFull, kmx);
+    __syncwarp();
+    const int top = 32 - __clz(kmn ^ kmx);
     int rank = cnt >> 1;
     unsigned mask = (top >= 32) ? 0u : ~((1u << top) - 1u);
-    unsigned prefix = kmin & mask;
+    unsigned prefix = kmn & mask;
     for (int hi = top; hi > 0; hi -= 8) {
         const int shift = hi >= 8 ? hi - 8 : 0;
         const int width = hi - shift;
         const unsigned dmask = (1u << width) - 1u;
-        rh[threadIdx.x] = 0;
-        __syncthreads();
-#pragma unroll
-        for (int r = 0; r < kSamplePer; r++)
-            if (ok[r] && (key[r] & mask) == prefix) atomicAdd(&rh[(key[r] >> shift) & dmask], 1);
-        __syncthreads();
-        const int h = rh[threadIdx.x];
-        int tot;
-        const int excl = block_excl_scan(h, sh, &tot);
-        if (h > 0 && rank >= excl && rank < excl + h) {
-            s_digit = threadIdx.x;
-            s_below = excl;
+        for (int b = lane; b < 256; b += 32) rh[b] = 0;
+        __syncwarp();
+#pragma unroll 4
+        for (int j = lane; j < cnt; j += 32) {
+            const unsigned key = float_key(__fadd_rn(vals[j], 0.0f));
+            if ((key & mask) == prefix) atomicAdd(&rh[(key >> shift) & dmask], 1);
         }
-        __syncthreads();
-        prefix |= (unsigned)s_digit << shift;
+        __syncwarp();
+        // lane t holds digits 8t .. 8t+7; the digit holding `rank` and the count below it
+        int loc = 0;
+#pragma unroll
+        for (int q = 0; q < 8; q++) loc += rh[8 * lane + q];
+        const int incl = warp_incl_scan(loc);
+        const int excl = incl - loc;
+        int found = -1, below = 0;
+        if (rank >= excl && rank < incl) {
+            int c = excl;
+            for (int q = 0; q < 8; q++) {
+                const int h = rh[8 * lane + q];
+                if (rank < c + h) {
+                    found = 8 * lane + q;
+                    below = c;
+                    break;
+                }
+                c += h;
+            }
+        }
+        const int src = __ffs(__ballot_sync(kFull, found >= 0)) - 1;
+        const int digit = __shfl_sync(kFull, found, src);
+        below = __shfl_sync(kFull, below, src);
+        prefix |= (unsigned)digit << shift;
         mask |= dmask << shift;
-        rank -= s_below;
-        __syncthreads();
+        rank -= below;
+        __syncwarp();
     }
     const float vp = key_float(prefix);
     int na = 0, nb = 0;
     float up = INFINITY;
-#pragma unroll
-    for (int r = 0; r < kSamplePer; r++) {
-        if (!ok[r]) continue;
-        const float x = xv[r];
+    for (int j = lane; j < cnt; j += 32) {
+        const float x = vals[j];
         na += x < vp;
         nb += x <= vp;
         if (x > vp) up = fminf(up, x);
     }
-    na = block_reduce_sum(na, sh);
-    nb = block_reduce_sum(nb, sh);
-    up = block_reduce_min(up, shf);
+    na = warp_sum(na);
+    nb = warp_sum(nb);
+    up = warp_min(up);
     long long e1 = 2LL * na - cnt;
     if (e1 < 0) e1 = -e1;
     float sv = vp;
@@ -513,12 +549,20 @@ __device__ void block_exact_split(const float* vals, int cnt, float* s_out, int*
             cv = nb;
         }
     }
-    *s_out = sv;
-    *c_out = cv;
+    if (lane == 0) {
+        if (cv > 0) {
+            a.nsplit[ai] = sv;
+            a.nleft[ai] = cv;
+            a.nsel[ai] = -1;
+            a.nmode[ai] = kModeSelected;
+        } else {
+            a.nmode[ai] = kModePending;   // heavy duplicates: k_select takes the fallback
+        }
+    }
 }
 
-// One block per active node: sample, per-dimension variance, split dimension,
-// bitonic sort of the sample along it.
+// One block per active node of more than kSamples points: sample, per-dimension
+// variance, split dimension, bitonic sort of the sample along it.
 
 __global__ void __launch_bounds__(kSampleThreads) k_sample(BuildArgs a, int L)
 {
@@ -532,15 +576,14 @@ __global__ void __launch_bounds__(kSampleThreads) k_sample(BuildArgs a, int L)
     if (ai >= a.cnt[kCntActive0 + cur]) return;
     const Active nd = a.act[cur][ai];
     const int cnt = nd.count;
-    const int sp = cnt < kSamples ? cnt : kSamples;
+    if (cnt <= kSamples) return;   // every point a sample: k_sample_small
+    const int sp = kSamples;
     const float* X = a.X[cur];
     for (int j = threadIdx.x; j < kSamples; j += blockDim.x) {
-        // floor(j * cnt / sp): j itself when sp = cnt, a shift when sp = 1024
-        const long long pos = nd.start + (sp == kSamples ? ((long long)j * cnt) >> 10 : (long long)j);
-        for (int k = 0; k < a.d; k++)
-            S[k * kSamples + j] = (j < sp) ? X[(long long)k * a.n_pad + pos] : INFINITY;
+        const long long pos = nd.start + (((long long)j * cnt) >> 10);   // floor(j * cnt / 1024)
+        for (int k = 0; k < a.d; k++) S[k * kSamples + j] = X[(long long)k * a.n_pad + pos];
     }
-    if (cnt > kSamples) {   // nodes of at most kSamples points are selected exactly below
+    {
         int* nh = a.nhist + (long long)ai * (kSamples + 1);
         for (int b = threadIdx.x; b <= kSamples; b += blockDim.x) nh[b] = 0;
     }
@@ -570,23 +613,6 @@ __global__ void __launch_bounds__(kSampleThreads) k_sample(BuildArgs a, int L)
     __syncthreads();
     const int dm = sdim;
     if (!(var[dm] > 0.0f)) return;
-    if (cnt <= kSamples) {
-        // every point is a sample: the exact selection (no sort, no histogram pass)
-        float sv;
-        int cv;
-        block_exact_split(S + dm * kSamples, cnt, &sv, &cv);
-        if (threadIdx.x == 0) {
-            if (cv > 0) {
-                a.nsplit[ai] = sv;
-                a.nleft[ai] = cv;
-                a.nsel[ai] = -1;
-                a.nmode[ai] = kModeSelected;
-            } else {
-                a.nmode[ai] = kModePending;   // heavy duplicates: k_select takes the fallback
-            }
-        }
-        return;
-    }
     // Bitonic sort.  Warp w takes the compare-exchange pairs kPairsPerWarp * w
     // onwards, which touch only its own 2 * kPairsPerWarp elements while the
     // stride is at most kPairsPerWarp: between two such stages a warp barrier
@@ -1747,6 +1773,7 @@ panda_status enqueue_level(BuildState& S, int L, cudaStream_t stream, PhaseTimer
     const int tcap = (int)std::min<long long>(pl.tile_cap, (long long)a.n / kTile + 2LL * acap + 2);
     timer.begin("level.sample");
     PANDA_LAUNCH(k_sample, acap, kSampleThreads, d * kSamples * 4, stream, a, L);
+    PANDA_LAUNCH(k_sample_small, (acap + kSmallWarps - 1) / kSmallWarps, kSmallWarps * 32, 0, stream, a, L);
     timer.begin("level.hist");
     PANDA_LAUNCH(k_hist, std::min(tcap, 8 * num_sms()), 256, 0, stream, a, L);
     timer.begin("level.select");

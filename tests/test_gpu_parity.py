@@ -230,7 +230,8 @@ def test_radius_errors(P):
 
 def test_self_host_async_pipelined(P):
     """Enqueue-only host results and stream-ordered frees, two steps in flight on
-    two streams: every step's host results equal the blocking call's."""
+    two streams, then with the builds on a third, high-priority stream: every
+    step's host results equal the blocking call's."""
     import torch
     pts = workloads.cosmology_points(120_000, seed=44, halos=20)
     pn = torch.from_numpy(pts).pin_memory().numpy()
@@ -246,6 +247,23 @@ def test_self_host_async_pipelined(P):
         tt = P.build_host(pn, 32, stream=s)
         P.knn_self_host(tt, 8, stream=s, out=outs[i], wait=False)
         tt.free(stream=s)
+    torch.cuda.synchronize()
+    for oi, od in outs:
+        assert_same_knn(oi, od, want_i, want_d)
+    # builds on a high-priority stream, each query and free on one of two
+    # normal-priority streams after an event on the build stream
+    lo, hi = torch.cuda.Stream.priority_range()
+    bs = torch.cuda.Stream(priority=hi)
+    qs = [torch.cuda.Stream(priority=lo), torch.cuda.Stream(priority=lo)]
+    for o in outs:
+        o[0].fill(0)
+    for i in range(4):
+        tt = P.build_host(pn, 32, stream=bs)
+        ev = torch.cuda.Event()
+        ev.record(bs)
+        qs[i % 2].wait_event(ev)
+        P.knn_self_host(tt, 8, stream=qs[i % 2], out=outs[i], wait=False)
+        tt.free(stream=qs[i % 2])
     torch.cuda.synchronize()
     for oi, od in outs:
         assert_same_knn(oi, od, want_i, want_d)
