@@ -303,6 +303,35 @@ def test_multilevel_cosmology_parity(P):
     assert t.info()["depth"] <= treecheck.balance_bound(pts.shape[0], 32)
 
 
+def test_lattice_duplicates_many_tiles(P):
+    """2^21 points on a 24^3 lattice (about 150 copies of every position) plus
+    a 2^20-point block of one repeated value: level passes over many tiles
+    with heavy ties, splits where the value rule leaves nothing on one side
+    (the duplicate fallback), nodes of identical points (index splits) and
+    windows of equal interval points.  Tree identical to the oracle's node by
+    node; sampled rows of a query set and of the all-points query against
+    exhaustive search."""
+    lat = workloads.lattice_points(1 << 21, 3, seed=41, side=24)
+    same = np.full((1 << 20, 3), 0.5, np.float32)
+    pts = np.concatenate([lat, same])[np.random.default_rng(42).permutation((1 << 21) + (1 << 20))]
+    q = workloads.lattice_points(20_000, 3, seed=43, side=24)
+    t = P.build(dev(pts), 32)
+    ot = oracle.build(pts, 32)
+    treecheck.assert_same_tree(t.export(), ot.export())
+    rows = np.arange(0, q.shape[0], 41)
+    ids, d2 = gpu_knn(P, t, q[rows], 12)
+    bi, bd = oracle.brute_knn(pts, q[rows], 12)
+    assert_same_knn(ids, d2, bi, bd)
+    # the all-points query (walks down to each job's leaf by the inner headers)
+    import torch
+    si, sd = P.knn_self(t, 12)
+    torch.cuda.synchronize()
+    prow = np.arange(0, pts.shape[0], 4099)
+    bi, bd = oracle.brute_knn(pts, pts, 12, rows=prow)
+    assert_same_knn(si.cpu().numpy()[prow], sd.cpu().numpy()[prow], bi, bd)
+    t.free()
+
+
 def test_plasma_slab_parity(P):
     pts = workloads.plasma_points(300_000, seed=4)
     q = workloads.plasma_points(20_000, seed=7)
