@@ -586,6 +586,19 @@ def run_ours(args):
                 "peak_source": f"{sms} SMs x 128 FP32 lanes x {sm_max:.0f} MHz (derived)",
                 "ms_per_launch": dom_ms / max(dom_launches, 1),
                 "kernel_counters": {"needed_nodes": int(v[0]), "needed_points": int(v[1]), **kstats}}
+        # the same launch against HBM: compulsory bytes (queries, result rows, the
+        # tree's points and node table, each moved once) and, where a capture
+        # exists, the DRAM bytes it measured
+        comp = (4 * d * m + 8 * k * m + n * (4 * d + 4)
+                + int(info["node_slots"]) * int(info["node_floats"]) * 4)
+        hbm_peak_q = float(peaks["hbm_gbs"])
+        launch_s = roof["ms_per_launch"] / 1e3
+        roof["hbm"] = {"compulsory_bytes": comp, "compulsory_gbs": comp / launch_s / 1e9,
+                       "frac": comp / launch_s / 1e9 / hbm_peak_q, "peak_gbs": hbm_peak_q,
+                       "traffic_gbs": (traffic / launch_s / 1e9) if traffic else None,
+                       "traffic_frac": (traffic / launch_s / 1e9 / hbm_peak_q) if traffic else None,
+                       "note": f"4d*m + 8k*m + n*(4d+4) + node table bytes per launch; peak of {peak_src} "
+                               f"STREAM-style copy"}
     # the build's streaming kernels against the HBM roofline (per step, all their launches)
     exp = t.export()
     act = level_active_points(exp, info["subtree_threshold"])
