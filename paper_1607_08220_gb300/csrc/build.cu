@@ -613,31 +613,64 @@ __global__ void __launch_bounds__(kSampleThreads) k_sample(BuildArgs a, int L)
     __syncthreads();
     const int dm = sdim;
     if (!(var[dm] > 0.0f)) return;
-    // Bitonic sort.  Warp w takes the compare-exchange pairs kPairsPerWarp * w
-    // onwards, which touch only its own 2 * kPairsPerWarp elements while the
-    // stride is at most kPairsPerWarp: between two such stages a warp barrier
-    // is enough, around the wider ones the block waits.
+    // Sort of the 1024 samples along dm.  First each warp sorts its own 128
+    // (bitonic network; warp w takes the compare-exchange pairs kPairsPerWarp * w
+    // onwards, which touch only its 128 elements, so warp barriers suffice) and
+    // leaves them ascending; then three rounds of merge-path merges (runs of
+    // 128 -> 256 -> 512 -> 1024) between the sample row and a second row: each
+    // thread finds where its 4 outputs start by a binary search of the
+    // diagonal and merges them.
     constexpr int kPairsPerWarp = kSamples / 2 / (kSampleThreads / 32);
+    constexpr int kRun = 2 * kPairsPerWarp;   // 128
     float* v = S + dm * kSamples;
-    for (int size = 2; size <= kSamples; size <<= 1) {
+    for (int size = 2; size <= kRun; size <<= 1) {
         for (int stride = size >> 1; stride > 0; stride >>= 1) {
 #pragma unroll
             for (int r = 0; r < kPairsPerWarp / 32; r++) {
                 const int t = warp * kPairsPerWarp + 32 * r + lane;
-                int i = 2 * t - (t & (stride - 1));
-                int j = i + stride;
-                bool up = (i & size) == 0;
-                float x = v[i], y = v[j];
+                const int i = 2 * t - (t & (stride - 1));
+                const int j = i + stride;
+                const bool up = size == kRun || (i & size) == 0;
+                const float x = v[i], y = v[j];
                 if ((x > y) == up) {
                     v[i] = y;
                     v[j] = x;
                 }
             }
-            const int next = stride > 1 ? stride >> 1 : (size < kSamples ? size : 2 * kSamples);
-            if (stride <= kPairsPerWarp && next <= kPairsPerWarp) __syncwarp();
-            else __syncthreads();
+            __syncwarp();
         }
     }
+    __syncthreads();
+    float* src = v;
+    float* dst = S + (a.d > 1 ? ((dm + 1) % a.d) : 1) * kSamples;   // a row no longer needed
+    for (int len = kRun; len < kSamples; len <<= 1) {
+        const int tpm = len / 2;                           // threads per merge: 4 outputs each
+        const int mi = threadIdx.x / tpm;
+        const int p = (threadIdx.x % tpm) * 4;
+        const float* A = src + mi * 2 * len;
+        const float* B = A + len;
+        // the diagonal's split: i outputs from A, p - i from B (A first on ties)
+        int lo = max(0, p - len), hi = min(p, len);
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (A[mid] <= B[p - mid - 1]) lo = mid + 1;
+            else hi = mid;
+        }
+        int i = lo, j = p - lo;
+        float* o = dst + mi * 2 * len + p;
+#pragma unroll
+        for (int e = 0; e < 4; e++) {
+            const bool takeA = j >= len || (i < len && A[i] <= B[j]);
+            o[e] = takeA ? A[i] : B[j];
+            i += takeA;
+            j += !takeA;
+        }
+        __syncthreads();
+        float* tmp = src;
+        src = dst;
+        dst = tmp;
+    }
+    v = src;
     float* out = a.vs + (long long)ai * kSamples;
     for (int j = threadIdx.x; j < kSamples; j += blockDim.x) out[j] = v[j];
 }
@@ -1772,7 +1805,7 @@ panda_status enqueue_level(BuildState& S, int L, cudaStream_t stream, PhaseTimer
                                                      : (1LL << 30), pl.act_cap);
     const int tcap = (int)std::min<long long>(pl.tile_cap, (long long)a.n / kTile + 2LL * acap + 2);
     timer.begin("level.sample");
-    PANDA_LAUNCH(k_sample, acap, kSampleThreads, d * kSamples * 4, stream, a, L);
+    PANDA_LAUNCH(k_sample, acap, kSampleThreads, std::max(d, 2) * kSamples * 4, stream, a, L);
     PANDA_LAUNCH(k_sample_small, (acap + kSmallWarps - 1) / kSmallWarps, kSmallWarps * 32, 0, stream, a, L);
     timer.begin("level.hist");
     PANDA_LAUNCH(k_hist, std::min(tcap, 8 * num_sms()), 256, 0, stream, a, L);
