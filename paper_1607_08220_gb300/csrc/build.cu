@@ -579,9 +579,19 @@ __global__ void __launch_bounds__(kSampleThreads) k_sample(BuildArgs a, int L)
     if (cnt <= kSamples) return;   // every point a sample: k_sample_small
     const int sp = kSamples;
     const float* X = a.X[cur];
-    for (int j = threadIdx.x; j < kSamples; j += blockDim.x) {
-        const long long pos = nd.start + (((long long)j * cnt) >> 10);   // floor(j * cnt / 1024)
-        for (int k = 0; k < a.d; k++) S[k * kSamples + j] = X[(long long)k * a.n_pad + pos];
+    // sample j at floor(j * cnt / 1024); a thread's four samples of a dimension
+    // are loaded before any is stored, so their (scattered) loads overlap
+    static_assert(kSamples == 4 * kSampleThreads, "four samples per thread");
+    long long pos[4];
+#pragma unroll
+    for (int r = 0; r < 4; r++) pos[r] = nd.start + (((long long)(threadIdx.x + r * kSampleThreads) * cnt) >> 10);
+    for (int k = 0; k < a.d; k++) {
+        const float* col = X + (long long)k * a.n_pad;
+        float x[4];
+#pragma unroll
+        for (int r = 0; r < 4; r++) x[r] = col[pos[r]];
+#pragma unroll
+        for (int r = 0; r < 4; r++) S[k * kSamples + threadIdx.x + r * kSampleThreads] = x[r];
     }
     {
         int* nh = a.nhist + (long long)ai * (kSamples + 1);
