@@ -47,6 +47,7 @@ struct BuildArgs {
     int tile_cap;
     int* tleft;
     int* tleftoff;
+    int* tbins;   // [tiles][1 + kWin]: a tile's count below the window, then its window bins
     float* vs;
     int* nhist;
     float* nvar;
@@ -751,10 +752,15 @@ __global__ void k_hist(BuildArgs a, int L)
         if (lane < qn) atomicAdd(&hist[count_le256(win, qw[lane]) - 1], 1);
         below = block_reduce_sum(below, sh);
         int* nh = a.nhist + (long long)ai * (kSamples + 1);
-        if (threadIdx.x == 0 && below) atomicAdd(&nh[kWinLo], below);
+        int* tb = a.tbins + (long long)t * (1 + kWin);   // this tile's own counts (k_tilecount)
+        if (threadIdx.x == 0) {
+            if (below) atomicAdd(&nh[kWinLo], below);
+            tb[0] = below;
+        }
         for (int b = threadIdx.x; b < kWin; b += blockDim.x) {
             const int h = hist[b];
             if (h) atomicAdd(&nh[kWinLo + 1 + b], h);
+            tb[1 + b] = h;
         }
         __syncthreads();
     }
@@ -840,7 +846,7 @@ __device__ void select_node(BuildArgs& a, int cur, int ai)
             if (threadIdx.x == 0) {
                 a.nsplit[ai] = a.vs[(long long)ai * kSamples + sel];
                 a.nleft[ai] = left;
-                a.nsel[ai] = sel;
+                a.nsel[ai] = FULL ? -1 : sel;   // >= 0: decided from the window bins
                 if (FULL) a.nmode[ai] = kModeValue;
             }
             return;
@@ -949,6 +955,16 @@ __global__ void k_tilecount(BuildArgs a, int L)
         if (a.nmode[ai] == kModeIndex) {
             const int half = (nd.count + 1) >> 1;
             if (threadIdx.x == 0) a.tleft[t] = min(max(half - (tl.begin - nd.start), 0), tl.end - tl.begin);
+            continue;
+        }
+        const int sel = a.nsel[ai];
+        if (sel >= kWinLo && sel <= kWinHi) {
+            // split v_sel from the window: the tile's x < v_sel are its points below
+            // v_kWinLo plus those in window bins kWinLo + 1 .. sel
+            const int* tb = a.tbins + (long long)t * (1 + kWin);
+            int c = (threadIdx.x < sel - kWinLo) ? tb[1 + threadIdx.x] : 0;
+            const int v = block_reduce_sum(c, sh);
+            if (threadIdx.x == 0) a.tleft[t] = tb[0] + v;
             continue;
         }
         const float s = a.nsplit[ai];
@@ -1741,6 +1757,7 @@ panda_status build_alloc(BuildState& S, int n, int d, cudaStream_t stream)
     }
     GET(a.tleft, (size_t)pl.tile_cap, "tile counts");
     GET(a.tleftoff, (size_t)pl.tile_cap, "tile offsets");
+    GET(a.tbins, (size_t)pl.tile_cap * (1 + kWin), "tile window bins");
     GET(a.vs, (size_t)pl.act_cap * kSamples, "samples");
     GET(a.nhist, (size_t)pl.act_cap * (kSamples + 1), "histograms");
     GET(a.nvar, (size_t)pl.act_cap * kMaxDim, "variances");
