@@ -1213,12 +1213,13 @@ __global__ void k_partition(BuildArgs a, int L)
         const bool in = i4 < tl.end;
         bool valid[4], left[4];
         float key[4] = {0.f, 0.f, 0.f, 0.f};
+        float4 kx4 = make_float4(0.f, 0.f, 0.f, 0.f);
         if (in) {
-            float4 x4 = *reinterpret_cast<const float4*>(Xs + dim * np + i4);
-            key[0] = x4.x;
-            key[1] = x4.y;
-            key[2] = x4.z;
-            key[3] = x4.w;
+            kx4 = *reinterpret_cast<const float4*>(Xs + dim * np + i4);
+            key[0] = kx4.x;
+            key[1] = kx4.y;
+            key[2] = kx4.z;
+            key[3] = kx4.w;
         }
         int nl = 0, nv = 0;
 #pragma unroll
@@ -1248,7 +1249,7 @@ __global__ void k_partition(BuildArgs a, int L)
         if (bad) atomicOr(a.err, kErrInternal);
         if (in) {
             for (int k = 0; k < a.d; k++) {
-                float4 v = *reinterpret_cast<const float4*>(Xs + k * np + i4);
+                const float4 v = k == dim ? kx4 : *reinterpret_cast<const float4*>(Xs + k * np + i4);
                 float* o = Xd + k * np;
                 if (valid[0]) o[dst[0]] = v.x;
                 if (valid[1]) o[dst[1]] = v.y;
