@@ -99,3 +99,28 @@ def test_window_rule_catches_a_wrong_window_check():
         j = int(np.argmin(np.abs(2 * c - n)))
         differs += (v[j], int(c[j])) != full_rule(x, v)
     assert differs > 0
+
+
+def test_tile_left_counts_from_window_bins():
+    """A tile's left count for a split decided in the window is its own count
+    below v_384 plus its window bins 385 .. j* (bin b: #{v_i <= x} = b), which
+    is how the build counts tiles without reading their column again."""
+    checked = 0
+    for x in nodes(9):
+        v = strided_sample(x)
+        if window_rule(x, v) is None:
+            continue
+        xs = np.sort(x)
+        c = np.searchsorted(xs, v, side="left")
+        j = int(np.argmin(np.abs(2 * c.astype(np.int64) - x.shape[0])))
+        if not (LO <= j <= HI):
+            continue
+        # cut the node at arbitrary tile boundaries
+        cuts = np.sort(np.random.default_rng(j).integers(0, x.shape[0], 5))
+        for t in np.split(x, cuts):
+            below = np.count_nonzero(t < v[LO])
+            b = np.searchsorted(v, t[(t >= v[LO]) & (t < v[HI])], side="right")
+            bins = np.bincount(b - LO - 1, minlength=HI - LO)
+            assert below + int(bins[: j - LO].sum()) == np.count_nonzero(t < v[j])
+            checked += 1
+    assert checked > 1000
